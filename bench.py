@@ -1,0 +1,371 @@
+"""Benchmark of the TNMC hot path on GB300: one step = one full pass over a batch of
+disorder realizations -- seeded +-J couplings, boundary-MPS environments (all rows cached),
+proposals with log q, Metropolis and observables.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Default workload (one GPU): L = 256, chi = 32, p = 0.109 on the Nishimori line,
+64 realizations x 2 chains x 250 proposals (500 proposals per realization), mixed precision
+(FP32 environment build, BF16 cached environments and sampling operands, FP64 log-norms,
+log q and Metropolis).  Under torchrun every rank runs its own 64 realizations (weak
+scaling, no data-path collective).  Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spins proposed/s at L=256 χ=32, BF16/TF32 vs FP64 GPU path; p50/p99 latency"
+UNIT = "spins/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["bf16", "tf32", "fp32", "fp64"])
+    ap.add_argument("--L", type=int, default=256)
+    ap.add_argument("--chi", type=int, default=32)
+    ap.add_argument("--R", type=int, default=64, help="realizations per GPU")
+    ap.add_argument("--n", type=int, default=250, help="proposals per chain per step")
+    ap.add_argument("--chains", type=int, default=2)
+    ap.add_argument("--p", type=float, default=0.109)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- oracle legs
+def _oracle_sample_worker(args):
+    """Time the oracle on a bounded sample of one realization: `rows` environment rows
+    (after the bond dimension has saturated) and the sampling sweep of those rows."""
+    L, chi, p, seed, rows = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    from oracle import boundary_mps as bm, lattice, sampler
+    beta = lattice.nishimori_beta(p)
+    Jh, Jv = lattice.split_couplings(lattice.couplings_pmj(seed, L, p), L)
+    Jh = Jh.astype(float); Jv = Jv.astype(float)
+    mps = [np.ones((1, 2, 1)) for _ in range(L)]
+    warm = int(math.ceil(math.log2(max(chi, 2)))) + 1
+    t_build = 0.0
+    built = []
+    for i, r in enumerate(range(L - 2, L - 2 - warm - rows, -1)):
+        t0 = time.perf_counter()
+        mps, _ = bm.compress(bm.apply_mpo(bm.row_mpo(beta, Jv[r], Jh[r + 1]), mps), chi)
+        dt = time.perf_counter() - t0
+        if i >= warm:
+            t_build += dt
+            built.append((r, mps))
+    t_samp = 0.0
+    K = 2
+    rng = np.random.default_rng(seed)
+    for r, m in built:
+        h = beta * Jv[r - 1][None, :] * np.where(rng.random((K, L)) < 0.5, 1.0, -1.0)
+        u = rng.random((K, L))
+        t0 = time.perf_counter()
+        sampler.sweep_row(m, Jh[r], h, beta, uniforms=u)
+        t_samp += time.perf_counter() - t0
+    return t_build / len(built), t_samp / (len(built) * K)
+
+
+def oracle_rate(L, chi, p, n_props_per_real, cores, budget_s):
+    """Spins proposed/s of the oracle on `cores` host processes, extrapolated from a bounded
+    sample: per-row environment cost and per-row-per-proposal sampling cost."""
+    import multiprocessing as mp
+    # size the sample: ~budget_s seconds per worker
+    rows = max(2, min(24, int(budget_s / max(1e-3, 0.6e-5 * L * chi ** 2))))
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_sample_worker, [(L, chi, p, 1000 + i, rows) for i in range(cores)])
+    wall = time.perf_counter() - t0
+    t_row = statistics.mean(r[0] for r in res)
+    t_srow = statistics.mean(r[1] for r in res)
+    t_real = (L - 1) * t_row + n_props_per_real * L * t_srow
+    rate = cores * n_props_per_real * L * L / t_real
+    sample = (f"{cores} processes x 1 realization each: {rows} environment rows (after bond saturation) and "
+              f"{rows} rows x 2 proposals of sampling, L={L} chi={chi}; extrapolated to {L - 1} rows + "
+              f"{n_props_per_real} proposals per realization (t_row={t_row:.3f}s, t_row_sample={t_srow * 1e3:.2f}ms)")
+    return rate, sample, wall
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    vals = []
+    sample = ""
+    for i in range(a.warmup + a.steps):
+        budget = max(3.0, a.cpu_seconds / 3)
+        rate, sample, _ = oracle_rate(a.L, a.chi, a.p, a.chains * a.n, cores, budget)
+        if i >= a.warmup:
+            vals.append(rate)
+    v = statistics.mean(vals)
+    spins_per_step = a.R * a.chains * a.n * a.L * a.L
+    line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=a.gpus, steps=a.steps, warmup=a.warmup,
+                ms_per_step=1e3 * spins_per_step / v, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic: Philox +-J disorder on the Nishimori line", impl="reference",
+                config=_config(a),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=cores, kind="oracle", sample=sample),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def _config(a):
+    return dict(workload=f"TNMC L={a.L} chi={a.chi} p={a.p} Nishimori beta, {a.R} realizations x "
+                         f"{a.chains} chains x {a.n} proposals per GPU per step",
+                L=a.L, chi=a.chi, p=a.p, realizations_per_gpu=a.R, chains=a.chains,
+                proposals_per_chain=a.n, precision=a.precision,
+                l2="inputs larger than L2: the environment cache read by the sampler is rebuilt every step")
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        load = [x for x in sm if x > 0.5 * mx] or sm
+        return dict(sm_mhz=statistics.median(load), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    a = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if a.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return _finish(world)
+
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2409_06538_gb300 as tn
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    beta = tn.nishimori_beta(a.p)
+    R, L = a.R, a.L
+
+    def seeds_for(step):
+        base = 1_000_003 * (step + 1) + rank * R
+        return np.arange(base, base + R, dtype=np.uint64)
+
+    J0 = tn.couplings_pmj(L, seeds_for(0), a.p, stream=stream)
+    ctx = tn.TNMC(L, J0, [beta] * R, seeds_for(0), a.chi, precision=a.precision, n_chains=a.chains,
+                  n_therm=0, stream=stream)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def one_step(step, marks=None):
+        s = seeds_for(step)
+        J = tn.couplings_pmj(L, s, a.p, stream=stream)
+        ctx.set_couplings(J, [beta] * R, s)
+        if marks: marks[0].record(stream)
+        ctx.build_env(return_logz=False)
+        if marks: marks[1].record(stream)
+        ctx.propose(a.n, 0, outputs=False)
+        if marks: marks[2].record(stream)
+        ctx.accept()
+        if marks: marks[3].record(stream)
+
+    for w in range(a.warmup):
+        one_step(w)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = ctx.launch_count()
+    t_start, t_end = ev(), ev()
+    step_ms, phases = [], []
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for k in range(a.steps):
+        m = [ev() for _ in range(4)]
+        s0 = ev(); s0.record(stream)
+        one_step(a.warmup + k, m)
+        s1 = ev(); s1.record(stream)
+        step_ms.append((s0, s1))
+        phases.append(m)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    # library launches in the timed region, plus the coupling generator kernel of each step
+    gpu_launches = ctx.launch_count() - launches0 + a.steps
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    clk = clocks.stop()
+    per_step = [s0.elapsed_time(s1) for s0, s1 in step_ms]
+    build_ms = statistics.mean(m[0].elapsed_time(m[1]) for m in phases)
+    samp_ms = statistics.mean(m[1].elapsed_time(m[2]) for m in phases)
+    acc_ms = statistics.mean(m[2].elapsed_time(m[3]) for m in phases)
+    obs = ctx.observables()
+    dav = tn.disorder_average(obs)
+    spins_per_step = R * a.chains * a.n * L * L
+    value = world * spins_per_step * a.steps / elapsed
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not a.no_e2e:
+        Jh_host = torch.empty((R, 2 * L * (L - 1)), dtype=torch.int8).pin_memory()
+        Jh_host.copy_(J0.cpu())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k_e2e = max(1, a.steps)
+        for k in range(k_e2e):
+            ctx.set_couplings(Jh_host, [beta] * R, seeds_for(0))
+            ctx.build_env(return_logz=False)
+            ctx.propose(a.n, 0, outputs=False)
+            ctx.accept()
+            _ = ctx.observables()
+        t1 = time.perf_counter()
+        e_el = t1 - t0
+        if world > 1:
+            t = torch.tensor([e_el], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_el = float(t.item())
+        e2e = dict(value=world * spins_per_step * k_e2e / e_el, unit=UNIT,
+                   h2d_bytes_per_step=int(R * 2 * L * (L - 1) + 16 * R),
+                   d2h_bytes_per_step=int(R * 112 + 8))
+
+    # ---- roofline of the dominant kernel
+    roof = roofline(a, build_ms, samp_ms, tn)
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        rate, sample, _ = oracle_rate(L, a.chi, a.p, a.chains * a.n, cores, a.cpu_seconds)
+        cpu = dict(value=rate, unit=UNIT, cores=cores, kind="oracle", sample=sample)
+
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=a.steps, warmup=a.warmup,
+                    ms_per_step=1e3 * elapsed / a.steps, higher_is_better=True, scaling="weak",
+                    vs_baseline=None, dtype=a.precision,
+                    data="synthetic: Philox +-J disorder on the Nishimori line (seeded, no dataset)",
+                    config=_config(a), e2e=e2e, gpu_launches=int(gpu_launches),
+                    roofline=roof, cpu_baseline=cpu, clocks=clk,
+                    latency_ms=dict(p50=float(np.percentile(per_step, 50)), p99=float(np.percentile(per_step, 99)),
+                                    unit="per batch of realizations (one step)"),
+                    phases_ms=dict(env_build=build_ms, propose=samp_ms, accept=acc_ms),
+                    accepted_proposals_per_s=value / (L * L) * dav["acceptance"],
+                    acceptance=dav["acceptance"], clamps=dav["clamps"],
+                    observables={k: dav[k] for k in ("E", "m2", "q2", "U_m", "Q_q")})
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return _finish(world)
+
+
+def roofline(a, build_ms, samp_ms, tn):
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    L, chi = a.L, a.chi
+    CHI = 4 if chi <= 4 else 8 if chi <= 8 else 16 if chi <= 16 else 32
+    te = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16": 2}[a.precision]
+    tw = 8 if a.precision == "fp64" else 4
+    items = a.chains * a.n
+    NW = 8
+    tiles = math.ceil(items / NW) * a.R
+    env_bytes = tiles * 2 * L * L * (2 * CHI * CHI) * te          # two sweeps per proposal tile
+    ws_bytes = a.R * items * L * L * (2 * CHI) * tw * 2            # workspace write + read
+    samp_bytes = env_bytes + ws_bytes
+    samp_gbs = samp_bytes / (samp_ms / 1e3) / 1e9
+    # FP32 ALU peak of the build: 152 SMs x 128 lanes x 2 flop x max clock
+    sm_clock = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    alu_peak = 152 * 128 * 2 * sm_clock / 1e12
+    if a.precision == "fp64":
+        alu_peak = alu_peak / 64.0
+    D = 2 * CHI
+    site_flops = (8 * D * D * CHI + (10.0 / 3.0) * D ** 3 + 4 * CHI ** 3 + 2 * D ** 3 + 2 * D * D * CHI
+                  + 6 * (D * (D - 1) / 2) * (12 * D))            # 6 Jacobi sweeps, nominal
+    build_flops = a.R * (L - 1) * L * site_flops
+    build_tf = build_flops / (build_ms / 1e3) / 1e12
+    dominant = "env_build" if build_ms >= samp_ms else "sample"
+    if dominant == "sample":
+        return dict(kernel="sample_kernel", bound="hbm", achieved=samp_gbs, peak=hbm, unit="GB/s",
+                    frac=samp_gbs / hbm, traffic=None, peak_source=src,
+                    algorithmic_bytes_per_launch=samp_bytes)
+    return dict(kernel="env_build_kernel", bound="alu", achieved=build_tf, peak=alu_peak, unit="TFLOP/s",
+                frac=build_tf / alu_peak, traffic=None,
+                peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock" + (" / 64 (FP64)" if a.precision == "fp64" else ""),
+                algorithmic_flops_per_launch=build_flops,
+                other={"sample_kernel_GBps": samp_gbs, "sample_frac_hbm": samp_gbs / hbm})
+
+
+def _finish(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * tnmc.h -- C ABI of the GB300 (sm_103a) Tensor Network Monte Carlo library for the
+ * two-dimensional +-J random-bond Ising model with open boundaries (arXiv 2409.06538).
+ *
+ * The library runs the three parts of the method on one GPU:
+ *   (a) the boundary-MPS contraction of the L x L partition-function network, row by row
+ *       from the bottom, with every row environment cached (Sec. II.B, Figs. 2-3);
+ *   (b) whole-lattice proposals drawn row by row from the conditionals those environments
+ *       give, with log q(s) (Sec. II.A Eqs. Bayes / approximate_bayes; Sec. II.B, Figs. 4-5);
+ *   (c) the Metropolis accept/reject against the Boltzmann weight (Eq. accptanceratio,
+ *       App. A) and the sampled observables (Sec. III.C).
+ *
+ * Conventions shared by every entry point
+ *   - Spin s = +1 or -1; in tensors index 0 <-> +1 and 1 <-> -1 (Sec. II.B copy tensor).
+ *   - Lattice L x L, site i = r*L + c (row r from the top, column c from the left).
+ *   - Couplings of one realization: 2L(L-1) int8 values +-1; first Jh[r][c] (bond
+ *     (r,c)-(r,c+1)) row-major over r<L, c<L-1, then Jv[r][c] (bond (r,c)-(r+1,c))
+ *     row-major over r<L-1, c<L.  E(s) = -sum J_ij s_i s_j (Eq. E).
+ *   - Random numbers: Philox4x32-10 keyed by the realization's 64-bit seed (low word
+ *     first); the uniform is ((x0>>5)*2^26 + (x1>>6)) * 2^-53 from the first two output
+ *     words.  Counters: bond b -> (b,0,0,0); spin at site i of proposal `step` of chain
+ *     `chain` -> (i, step, chain, 1); accept test of that proposal -> (0, step, chain, 2).
+ *   - Pointers named *_dev are device pointers on the context's CUDA device; *_host are
+ *     host pointers; "host or device" pointers are classified by cudaPointerGetAttributes.
+ *     The caller owns every buffer it passes; the library copies inputs at the call and
+ *     never keeps a caller pointer.
+ *   - Every call returns a tnmc_status and never aborts the process.  Work is queued on the
+ *     context's stream (opts.stream, a cudaStream_t, NULL = legacy default stream); calls
+ *     that return host data synchronise that stream.  Device-side failures (a vanishing or
+ *     non-finite conditional weight, a wait that ran out) are recorded in a device status
+ *     word and returned by the next synchronising call; tnmc_last_error() gives the text.
+ *   - Order of use: create -> build_env -> (propose -> accept)* -> observables -> destroy.
+ *     Out-of-order use returns TNMC_ERR_STATE.
+ */
+#ifndef TNMC_H
+#define TNMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TNMC_OK = 0,
+  TNMC_ERR_ARG = 1,         /* invalid argument (sizes, NULL where not allowed, |J| != 1, ...) */
+  TNMC_ERR_OOM = 2,         /* device allocation failed */
+  TNMC_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+  TNMC_ERR_NUMERIC = 4,     /* w(+)+w(-) <= 0 or not finite at some site (oracle reading: error) */
+  TNMC_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
+  TNMC_ERR_STATE = 6,       /* call out of order (e.g. propose before build_env) */
+  TNMC_ERR_UNSUPPORTED = 7  /* configuration not built into this library (e.g. chi > 32) */
+} tnmc_status;
+
+typedef enum {
+  TNMC_FP64 = 0,        /* everything in FP64 */
+  TNMC_FP32 = 1,        /* environments built and stored in FP32, sampling in FP32 */
+  TNMC_MIXED_BF16 = 2,  /* FP32 build, BF16 cached environments, BF16 tensor-core sampling
+                           GEMMs with FP32 accumulation; log-norms and log q in FP64 */
+  TNMC_MIXED_TF32 = 3   /* FP32 build and cache, TF32 tensor-core sampling GEMMs */
+} tnmc_precision;
+
+typedef struct {
+  int precision;      /* tnmc_precision */
+  int n_chains;       /* Markov chains (replicas) per realization, >= 1; the overlap q of
+                         Sec. III.C is measured between chains 0 and 1 when n_chains >= 2 */
+  int n_therm;        /* steps with global step index < n_therm are not measured */
+  void* stream;       /* cudaStream_t for all work of this context; NULL = default stream */
+} tnmc_opts;
+
+/* Per-realization thermal means over measured steps (Sec. III.C).  m = (1/N) sum_i s_i,
+ * q = (1/N) sum_i s_i^(0) s_i^(1) between the current states of chains 0 and 1 at the same
+ * step; E, m statistics pool all chains. */
+typedef struct {
+  int64_t n_prop;       /* proposals processed by accept (all chains) */
+  int64_t n_acc;        /* proposals accepted (excluding each chain's unconditional first) */
+  int64_t n_meas;       /* measured (chain, step) pairs */
+  int64_t n_meas_q;     /* measured steps for the overlap */
+  int64_t clamps;       /* negative truncated weights clamped to zero while sampling */
+  double E, E2, m_abs, m2, m4;
+  double q, q_abs, q2, q4;
+} tnmc_obs;
+
+typedef struct tnmc_ctx tnmc_ctx;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int tnmc_version(void);
+
+/* Seeded synthetic disorder (Sec. III.A, P(J) = (1-p) delta(J-1) + p delta(J+1)):
+ * J_b = -1 iff u_b < p with u_b the Philox uniform of counter (b,0,0,0) under seeds[k].
+ * Writes n_real * 2L(L-1) int8 couplings to out_dev (device) in the layout above.
+ * Errors: TNMC_ERR_ARG for L < 2, n_real < 1, p outside [0,1] or NULL pointers. */
+tnmc_status tnmc_couplings_pmj(int L, int n_real, const uint64_t* seeds_host, double p,
+                               int8_t* out_dev, void* stream);
+
+/* Create a context for n_real independent disorder realizations of one lattice size L
+ * and one cut-off bond dimension chi (the "cutoff bond dimension of the matrix product
+ * states", D in Table tableparameter).
+ *   couplings : host or device, n_real * 2L(L-1) int8 +-1 (copied);
+ *   beta_host : n_real inverse temperatures (Eq. P); on the Nishimori line
+ *               beta = 0.5 ln((1-p)/p) (Sec. III.A);
+ *   seeds_host: n_real Philox keys for the spin and accept draws;
+ *   chi       : 1 <= chi <= 32.
+ * Allocates the environment cache (n_real * L * L * 2 chi^2 words) and all scratch on the
+ * current CUDA device.  Errors: TNMC_ERR_ARG, TNMC_ERR_OOM, TNMC_ERR_UNSUPPORTED, TNMC_ERR_CUDA. */
+tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double* beta_host,
+                        const uint64_t* seeds_host, int chi, const tnmc_opts* opts,
+                        tnmc_ctx** out);
+
+/* Replace the disorder realizations of an existing context (same L, n_real, chi): copies
+ * new couplings (host or device), inverse temperatures and seeds, resets the chains and
+ * marks the environments stale.  Lets one context serve successive batches without
+ * re-allocating its caches.  Errors as tnmc_create. */
+tnmc_status tnmc_set_couplings(tnmc_ctx* ctx, const int8_t* couplings, const double* beta_host,
+                               const uint64_t* seeds_host);
+
+/* (a) Boundary-MPS contraction (Sec. II.B): for r = L-2 .. 0 apply the row-transfer MPO
+ * (the T tensors: copy tensor with the Boltzmann matrices W absorbed) to the cached MPS of
+ * row r+1, cut the bond dimension back to chi by SVD (keeping min(chi, rows, cols) singular
+ * values at every bond, swept right to left from left-canonical form), normalise, and cache
+ * the row with its FP64 log-norm.  log_z_host (nullable, n_real doubles) receives log Z of the
+ * truncated network (exact when nothing is truncated); passing it synchronises. */
+tnmc_status tnmc_build_env(tnmc_ctx* ctx, double* log_z_host);
+
+/* (b) Draw n proposals per chain (global step indices step0 .. step0+n-1) from the cached
+ * environments, row by row top to bottom and left to right (Sec. II.B), with log q(s) in
+ * FP64 and the exact integer energy.  Proposals stay on the device for tnmc_accept.
+ * Optional device outputs (each nullable), index [real][chain][k]:
+ *   logq_dev (double), energy_dev (int32), magnet_dev (int32 sum of spins). */
+tnmc_status tnmc_propose(tnmc_ctx* ctx, int n, uint64_t step0, double* logq_dev,
+                         int32_t* energy_dev, int32_t* magnet_dev);
+
+/* Unpack the spins of the last tnmc_propose call to spins_dev (device int8 +-1,
+ * [real][chain][k][L*L]). */
+tnmc_status tnmc_get_spins(tnmc_ctx* ctx, int8_t* spins_dev);
+
+/* Teacher-forced evaluation of q on given configurations (the conditionals of Eq. cond
+ * from the cached environments, with the given spins in place of draws).
+ *   spins_dev: device int8 +-1, [real][k][L*L], n configurations per realization;
+ *   logq_dev : device double [real][k] (nullable);
+ *   qplus_dev: device double [real][k][L*L], q(s_i=+1 | s_<i) at every site (nullable). */
+tnmc_status tnmc_eval_conditionals(tnmc_ctx* ctx, int n, const int8_t* spins_dev,
+                                   double* logq_dev, double* qplus_dev);
+
+/* (c) Metropolis accept/reject over the proposals of the last tnmc_propose call, in step
+ * order per chain (Eq. accptanceratio with g(s'|s) = q(s')):
+ *   Delta = [-beta E(s') - log q(s')] - [-beta E(s) - log q(s)],
+ *   accept iff Delta >= 0 or u < exp(Delta).
+ * A chain's first proposal ever is its initial state.  The current state carries over to
+ * the next call.  Observables of every step with global index >= opts.n_therm accumulate.
+ *   accepted_dev  : device uint8 [real][chain][k] (nullable);
+ *   n_accepted_host: total accepted in this call (nullable; passing it synchronises). */
+tnmc_status tnmc_accept(tnmc_ctx* ctx, uint8_t* accepted_dev, int64_t* n_accepted_host);
+
+/* Per-realization thermal means (host array of n_real tnmc_obs).  Synchronises. */
+tnmc_status tnmc_observables(tnmc_ctx* ctx, tnmc_obs* out_host);
+
+/* Reset chain states and observable accumulators (the environments stay cached). */
+tnmc_status tnmc_reset_chains(tnmc_ctx* ctx);
+
+/* Release every device allocation of the context.  NULL is accepted. */
+tnmc_status tnmc_destroy(tnmc_ctx* ctx);
+
+/* Text of the last error on this context (or of the last failed create when ctx is NULL). */
+const char* tnmc_last_error(const tnmc_ctx* ctx);
+
+/* Introspection used by tests and the benchmark.
+ *   tnmc_env_bytes: bytes of the environment cache;
+ *   tnmc_copy_env : copy the cached environment of (real, row) to host: tiles_host gets
+ *                   L * 2 * chi * chi doubles ([c][y][alpha][beta], zero padded),
+ *                   dims_host gets the L+1 bond dimensions, lam_host the row log-norm. */
+size_t tnmc_env_bytes(const tnmc_ctx* ctx);
+tnmc_status tnmc_copy_env(tnmc_ctx* ctx, int real, int row, double* tiles_host,
+                          int32_t* dims_host, double* lam_host);
+
+/* Statistics of the last tnmc_build_env, summed over realizations: out_host[0] = most
+ * Jacobi sweeps any truncation needed, [1] = truncations that hit the sweep limit,
+ * [2] = total sweeps, [3] = truncating SVDs performed.  Synchronises. */
+tnmc_status tnmc_build_stats(tnmc_ctx* ctx, int64_t* out_host);
+
+/* Kernel launch accounting: number of kernels this context launched since creation. */
+int64_t tnmc_launch_count(const tnmc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNMC_H */

@@ -1,0 +1,84 @@
+"""ctypes declarations of the C ABI in include/tnmc.h.  Marshalling only: every step of the
+method runs in libtnmc.so.  Importing fails loudly when the library has not been built;
+there is no fallback implementation."""
+import ctypes
+import os
+
+from . import buildlib as _build
+
+c_int, c_int64, c_size_t, c_double, c_void_p = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_double, ctypes.c_void_p
+c_uint64_p = ctypes.POINTER(ctypes.c_uint64)
+c_double_p = ctypes.POINTER(ctypes.c_double)
+c_int32_p = ctypes.POINTER(ctypes.c_int32)
+c_int64_p = ctypes.POINTER(ctypes.c_int64)
+
+STATUS = {0: "TNMC_OK", 1: "TNMC_ERR_ARG", 2: "TNMC_ERR_OOM", 3: "TNMC_ERR_CUDA", 4: "TNMC_ERR_NUMERIC",
+          5: "TNMC_ERR_TIMEOUT", 6: "TNMC_ERR_STATE", 7: "TNMC_ERR_UNSUPPORTED"}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "tf32": 3}
+
+# Entry points declared in include/tnmc.h: name -> (restype, argtypes)
+SIGNATURES = {
+    "tnmc_version": (c_int, []),
+    "tnmc_couplings_pmj": (c_int, [c_int, c_int, c_uint64_p, c_double, c_void_p, c_void_p]),
+    "tnmc_create": (c_int, [c_int, c_int, c_void_p, c_double_p, c_uint64_p, c_int, c_void_p,
+                            ctypes.POINTER(c_void_p)]),
+    "tnmc_set_couplings": (c_int, [c_void_p, c_void_p, c_double_p, c_uint64_p]),
+    "tnmc_build_env": (c_int, [c_void_p, c_double_p]),
+    "tnmc_propose": (c_int, [c_void_p, c_int, ctypes.c_uint64, c_void_p, c_void_p, c_void_p]),
+    "tnmc_get_spins": (c_int, [c_void_p, c_void_p]),
+    "tnmc_eval_conditionals": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "tnmc_accept": (c_int, [c_void_p, c_void_p, c_int64_p]),
+    "tnmc_observables": (c_int, [c_void_p, c_void_p]),
+    "tnmc_reset_chains": (c_int, [c_void_p]),
+    "tnmc_destroy": (c_int, [c_void_p]),
+    "tnmc_last_error": (ctypes.c_char_p, [c_void_p]),
+    "tnmc_env_bytes": (c_size_t, [c_void_p]),
+    "tnmc_copy_env": (c_int, [c_void_p, c_int, c_int, c_double_p, c_int32_p, c_double_p]),
+    "tnmc_launch_count": (c_int64, [c_void_p]),
+    "tnmc_build_stats": (c_int, [c_void_p, c_int64_p]),
+}
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("n_chains", c_int), ("n_therm", c_int), ("stream", c_void_p)]
+
+
+class Obs(ctypes.Structure):
+    _fields_ = [("n_prop", c_int64), ("n_acc", c_int64), ("n_meas", c_int64), ("n_meas_q", c_int64),
+                ("clamps", c_int64), ("E", c_double), ("E2", c_double), ("m_abs", c_double),
+                ("m2", c_double), ("m4", c_double), ("q", c_double), ("q_abs", c_double),
+                ("q2", c_double), ("q4", c_double)]
+
+
+class TnmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_LIB = None
+
+
+def load(path=None):
+    """Load libtnmc.so (built in-tree by __graft_entry__.build() / build.py)."""
+    global _LIB
+    if _LIB is not None and path is None:
+        return _LIB
+    p = path or _build.lib_path()
+    if not os.path.exists(p):
+        raise ImportError(f"libtnmc.so is not built ({p}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _LIB = lib
+    return lib
+
+
+def check(code, ctx=None):
+    if code != 0:
+        lib = load()
+        msg = lib.tnmc_last_error(ctx)
+        raise TnmcError(code, msg.decode() if msg else "")

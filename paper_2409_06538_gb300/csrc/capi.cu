@@ -1,0 +1,493 @@
+// C ABI of the TNMC library (declared in include/tnmc.h): context lifetime, device memory,
+// argument checking and kernel launches.  No torch types cross this boundary.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tnmc.h"
+#include "kernels.h"
+
+struct tnmc_ctx {
+  int L = 0, n_real = 0, chi = 0, CHI = 0, precision = 0, n_chains = 1, n_therm = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 0;
+  std::string err;
+  int64_t launches = 0;
+  int words = 0;
+  // inputs
+  int8_t* J = nullptr;
+  double* beta = nullptr;
+  uint64_t* seeds = nullptr;
+  // environments
+  void* env = nullptr;
+  size_t env_bytes = 0, te_size = 0, t_size = 0;
+  int* kdim = nullptr;
+  int* dqr = nullptr;
+  double* lam = nullptr;
+  double* logz = nullptr;
+  void* rowbuf = nullptr;
+  void* Rstore = nullptr;
+  long long* stats = nullptr;
+  unsigned* status = nullptr;
+  // sampling
+  void* work = nullptr;
+  uint32_t* packed = nullptr;
+  double* logq = nullptr;
+  int32_t* energy = nullptr;
+  int32_t* magnet = nullptr;
+  int64_t* clamps = nullptr;
+  int cap_n = 0;
+  int last_n = 0;
+  uint64_t last_step0 = 0;
+  bool have_props = false;
+  bool env_built = false;
+  // chains
+  int* have_state = nullptr;
+  double* cur_logq = nullptr;
+  int32_t* cur_energy = nullptr;
+  int32_t* cur_magnet = nullptr;
+  uint32_t* cur_spins = nullptr;
+  double* acc = nullptr;
+  int* cur_idx = nullptr;
+  std::vector<void*> allocs;
+};
+
+static std::string g_create_err;
+
+namespace {
+
+tnmc_status fail(tnmc_ctx* c, tnmc_status s, const std::string& msg) {
+  if (c) c->err = msg; else g_create_err = msg;
+  return s;
+}
+
+tnmc_status cuda_fail(tnmc_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, TNMC_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename P>
+tnmc_status dalloc(tnmc_ctx* c, P** p, size_t bytes) {
+  void* q = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, TNMC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                     cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  *p = reinterpret_cast<P*>(q);
+  return TNMC_OK;
+}
+
+void dfree(tnmc_ctx* c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c->allocs.size(); ++i)
+    if (c->allocs[i] == p) { c->allocs.erase(c->allocs.begin() + i); break; }
+  cudaFree(p);
+}
+
+int round_chi(int chi) {
+  if (chi <= 4) return 4;
+  if (chi <= 8) return 8;
+  if (chi <= 16) return 16;
+  if (chi <= 32) return 32;
+  return 0;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+tnmc_status check_status(tnmc_ctx* c) {
+  unsigned st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+  if (st & tnmc::ST_NUMERIC)
+    return fail(c, TNMC_ERR_NUMERIC, "a conditional weight w(+)+w(-) vanished or was not finite");
+  if (st & tnmc::ST_TIMEOUT) return fail(c, TNMC_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (st & tnmc::ST_ARG) return fail(c, TNMC_ERR_ARG, "a kernel rejected its arguments");
+  return TNMC_OK;
+}
+
+tnmc_status ensure_props(tnmc_ctx* c, int n) {
+  if (n <= c->cap_n) return TNMC_OK;
+  dfree(c, c->packed); dfree(c, c->logq); dfree(c, c->energy); dfree(c, c->magnet); dfree(c, c->cur_idx);
+  c->packed = nullptr; c->logq = nullptr; c->energy = nullptr; c->magnet = nullptr; c->cur_idx = nullptr;
+  const size_t items = (size_t)c->n_real * c->n_chains * n;
+  tnmc_status s;
+  if ((s = dalloc(c, &c->packed, items * c->words * sizeof(uint32_t)))) return s;
+  if ((s = dalloc(c, &c->logq, items * sizeof(double)))) return s;
+  if ((s = dalloc(c, &c->energy, items * sizeof(int32_t)))) return s;
+  if ((s = dalloc(c, &c->magnet, items * sizeof(int32_t)))) return s;
+  if ((s = dalloc(c, &c->cur_idx, items * sizeof(int)))) return s;
+  c->cap_n = n;
+  return TNMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tnmc_version(void) { return 100; }
+
+const char* tnmc_last_error(const tnmc_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+tnmc_status tnmc_couplings_pmj(int L, int n_real, const uint64_t* seeds_host, double p, int8_t* out_dev,
+                               void* stream) {
+  if (L < 2 || n_real < 1 || !seeds_host || !out_dev || !(p >= 0.0 && p <= 1.0))
+    return fail(nullptr, TNMC_ERR_ARG, "tnmc_couplings_pmj: invalid argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint64_t* sd = nullptr;
+  cudaError_t e = cudaMalloc(&sd, sizeof(uint64_t) * n_real);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, TNMC_ERR_OOM, "seed buffer"); }
+  e = cudaMemcpyAsync(sd, seeds_host, sizeof(uint64_t) * n_real, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = tnmc::launch_couplings(L, n_real, sd, p, out_dev, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(sd);
+  if (e != cudaSuccess) return fail(nullptr, TNMC_ERR_CUDA, std::string("couplings: ") + cudaGetErrorString(e));
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double* beta_host,
+                        const uint64_t* seeds_host, int chi, const tnmc_opts* opts, tnmc_ctx** out) {
+  if (!out) return fail(nullptr, TNMC_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (L < 2 || L > 4096) return fail(nullptr, TNMC_ERR_ARG, "L must be in [2, 4096]");
+  if (n_real < 1) return fail(nullptr, TNMC_ERR_ARG, "n_real must be >= 1");
+  if (!couplings || !beta_host || !seeds_host || !opts) return fail(nullptr, TNMC_ERR_ARG, "NULL input");
+  if (chi < 1) return fail(nullptr, TNMC_ERR_ARG, "chi must be >= 1");
+  if (round_chi(chi) == 0) return fail(nullptr, TNMC_ERR_UNSUPPORTED, "chi > 32 is not built into this library");
+  if (opts->precision < 0 || opts->precision > 3) return fail(nullptr, TNMC_ERR_ARG, "unknown precision");
+  if (opts->n_chains < 1 || opts->n_chains > 8) return fail(nullptr, TNMC_ERR_ARG, "n_chains must be in [1, 8]");
+  for (int k = 0; k < n_real; ++k)
+    if (!(beta_host[k] > 0.0) || !std::isfinite(beta_host[k]))
+      return fail(nullptr, TNMC_ERR_ARG, "beta must be positive and finite");
+  const size_t nb = (size_t)2 * L * (L - 1);
+  std::vector<int8_t> Jh(nb * n_real);
+  if (cudaMemcpy(Jh.data(), couplings, Jh.size(), cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, TNMC_ERR_ARG, "couplings pointer is neither host nor device memory");
+  }
+  for (size_t i = 0; i < Jh.size(); ++i)
+    if (Jh[i] != 1 && Jh[i] != -1) return fail(nullptr, TNMC_ERR_ARG, "couplings must be +1 or -1");
+
+  tnmc_ctx* c = new tnmc_ctx();
+  c->L = L; c->n_real = n_real; c->chi = chi; c->CHI = round_chi(chi);
+  c->precision = opts->precision; c->n_chains = opts->n_chains; c->n_therm = opts->n_therm;
+  c->stream = reinterpret_cast<cudaStream_t>(opts->stream);
+  c->words = (L * L + 31) / 32;
+  cudaGetDevice(&c->device);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  c->t_size = c->precision == TNMC_FP64 ? 8 : 4;
+  c->te_size = c->precision == TNMC_FP64 ? 8 : (c->precision == TNMC_MIXED_BF16 ? 2 : 4);
+  const int CHI = c->CHI, D = 2 * CHI;
+  const size_t tile = (size_t)2 * CHI * CHI;
+  tnmc_status s;
+#define TRY(x) do { if ((s = (x)) != TNMC_OK) { g_create_err = c->err; tnmc_destroy(c); return s; } } while (0)
+  TRY(dalloc(c, &c->J, nb * n_real));
+  TRY(dalloc(c, &c->beta, sizeof(double) * n_real));
+  TRY(dalloc(c, &c->seeds, sizeof(uint64_t) * n_real));
+  c->env_bytes = (size_t)n_real * L * L * tile * c->te_size;
+  TRY(dalloc(c, &c->env, c->env_bytes));
+  TRY(dalloc(c, &c->kdim, sizeof(int) * (size_t)n_real * L * (L + 1)));
+  TRY(dalloc(c, &c->dqr, sizeof(int) * (size_t)n_real * (L + 1)));
+  TRY(dalloc(c, &c->lam, sizeof(double) * (size_t)n_real * L));
+  TRY(dalloc(c, &c->logz, sizeof(double) * n_real));
+  TRY(dalloc(c, &c->rowbuf, (size_t)n_real * 2 * L * tile * c->t_size));
+  TRY(dalloc(c, &c->Rstore, (size_t)n_real * L * D * D * c->t_size));
+  TRY(dalloc(c, &c->stats, sizeof(long long) * 4 * n_real));
+  TRY(dalloc(c, &c->status, sizeof(unsigned)));
+  TRY(dalloc(c, &c->work, tnmc::sample_work_bytes(L, CHI, c->precision, c->num_sms)));
+  TRY(dalloc(c, &c->clamps, sizeof(int64_t) * n_real));
+  const size_t chains = (size_t)n_real * c->n_chains;
+  TRY(dalloc(c, &c->have_state, sizeof(int) * chains));
+  TRY(dalloc(c, &c->cur_logq, sizeof(double) * chains));
+  TRY(dalloc(c, &c->cur_energy, sizeof(int32_t) * chains));
+  TRY(dalloc(c, &c->cur_magnet, sizeof(int32_t) * chains));
+  TRY(dalloc(c, &c->cur_spins, sizeof(uint32_t) * chains * c->words));
+  TRY(dalloc(c, &c->acc, sizeof(double) * (size_t)n_real * tnmc::ACC_SLOTS));
+#undef TRY
+  cudaError_t e = cudaMemcpyAsync(c->J, Jh.data(), Jh.size(), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->beta, beta_host, sizeof(double) * n_real, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->seeds, seeds_host, sizeof(uint64_t) * n_real, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->clamps, 0, sizeof(int64_t) * n_real, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->have_state, 0, sizeof(int) * chains, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(double) * (size_t)n_real * tnmc::ACC_SLOTS, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) { cuda_fail(c, e, "create"); g_create_err = c->err; tnmc_destroy(c); return TNMC_ERR_CUDA; }
+  *out = c;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_set_couplings(tnmc_ctx* c, const int8_t* couplings, const double* beta_host,
+                               const uint64_t* seeds_host) {
+  if (!c || !couplings || !beta_host || !seeds_host) return fail(c, TNMC_ERR_ARG, "NULL argument");
+  for (int k = 0; k < c->n_real; ++k)
+    if (!(beta_host[k] > 0.0) || !std::isfinite(beta_host[k])) return fail(c, TNMC_ERR_ARG, "beta must be positive and finite");
+  const size_t nb = (size_t)2 * c->L * (c->L - 1) * c->n_real;
+  cudaError_t e;
+  if (is_device_ptr(couplings)) {
+    e = cudaMemcpyAsync(c->J, couplings, nb, cudaMemcpyDeviceToDevice, c->stream);
+  } else {
+    for (size_t i = 0; i < nb; ++i)
+      if (couplings[i] != 1 && couplings[i] != -1) return fail(c, TNMC_ERR_ARG, "couplings must be +1 or -1");
+    e = cudaMemcpyAsync(c->J, couplings, nb, cudaMemcpyHostToDevice, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->beta, beta_host, sizeof(double) * c->n_real, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->seeds, seeds_host, sizeof(uint64_t) * c->n_real, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set couplings");
+  c->env_built = false;
+  return tnmc_reset_chains(c);
+}
+
+tnmc_status tnmc_build_env(tnmc_ctx* c, double* log_z_host) {
+  if (!c) return fail(nullptr, TNMC_ERR_ARG, "NULL context");
+  cudaError_t e;
+  switch (c->precision) {
+    case TNMC_FP64: {
+      tnmc::EnvBuildArgs<double, double> a{c->L, c->n_real, c->chi, c->J, c->beta, (double*)c->env, c->kdim, c->dqr,
+                                           c->lam, c->logz, (double*)c->rowbuf, (double*)c->Rstore, c->stats, c->status};
+      e = tnmc::launch_env_build(a, c->CHI, c->stream);
+      break;
+    }
+    case TNMC_MIXED_BF16: {
+      tnmc::EnvBuildArgs<float, __nv_bfloat16> a{c->L, c->n_real, c->chi, c->J, c->beta, (__nv_bfloat16*)c->env, c->kdim,
+                                                 c->dqr, c->lam, c->logz, (float*)c->rowbuf, (float*)c->Rstore, c->stats, c->status};
+      e = tnmc::launch_env_build(a, c->CHI, c->stream);
+      break;
+    }
+    default: {
+      tnmc::EnvBuildArgs<float, float> a{c->L, c->n_real, c->chi, c->J, c->beta, (float*)c->env, c->kdim, c->dqr,
+                                         c->lam, c->logz, (float*)c->rowbuf, (float*)c->Rstore, c->stats, c->status};
+      e = tnmc::launch_env_build(a, c->CHI, c->stream);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "env build launch");
+  ++c->launches;
+  c->env_built = true;
+  if (log_z_host) {
+    tnmc_status s = check_status(c);
+    if (s) return s;
+    e = cudaMemcpy(log_z_host, c->logz, sizeof(double) * c->n_real, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "log Z copy");
+  }
+  return TNMC_OK;
+}
+
+static tnmc_status run_sample(tnmc_ctx* c, int n, uint64_t step0, const int8_t* forced, double* logq,
+                              double* qplus, bool props) {
+  tnmc::SampleArgs a{};
+  a.L = c->L; a.n_real = c->n_real; a.n_chains = props ? c->n_chains : 1; a.n = n;
+  a.n_items = props ? c->n_chains * n : n;
+  a.step0 = step0; a.J = c->J; a.beta = c->beta; a.seeds = c->seeds; a.env = c->env;
+  a.spins_packed = props ? c->packed : nullptr; a.words = c->words;
+  a.logq = logq; a.energy = props ? c->energy : nullptr; a.magnet = props ? c->magnet : nullptr;
+  a.clamps = props ? c->clamps : nullptr; a.forced = forced; a.qplus = qplus; a.work = c->work;
+  a.status = c->status;
+  cudaError_t e = tnmc::launch_sample(a, c->precision, c->CHI, c->num_sms, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "sample launch");
+  ++c->launches;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_propose(tnmc_ctx* c, int n, uint64_t step0, double* logq_dev, int32_t* energy_dev,
+                         int32_t* magnet_dev) {
+  if (!c) return fail(nullptr, TNMC_ERR_ARG, "NULL context");
+  if (!c->env_built) return fail(c, TNMC_ERR_STATE, "tnmc_propose before tnmc_build_env");
+  if (n < 1) return fail(c, TNMC_ERR_ARG, "n must be >= 1");
+  if (step0 + (uint64_t)n > 0xFFFFFFFFull) return fail(c, TNMC_ERR_ARG, "step indices must fit in 32 bits");
+  tnmc_status s = ensure_props(c, n);
+  if (s) return s;
+  if ((s = run_sample(c, n, step0, nullptr, c->logq, nullptr, true))) return s;
+  const size_t items = (size_t)c->n_real * c->n_chains * n;
+  cudaError_t e = cudaSuccess;
+  if (logq_dev) e = cudaMemcpyAsync(logq_dev, c->logq, items * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess && energy_dev)
+    e = cudaMemcpyAsync(energy_dev, c->energy, items * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess && magnet_dev)
+    e = cudaMemcpyAsync(magnet_dev, c->magnet, items * sizeof(int32_t), cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "propose output copy");
+  c->last_n = n; c->last_step0 = step0; c->have_props = true;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_get_spins(tnmc_ctx* c, int8_t* spins_dev) {
+  if (!c || !spins_dev) return fail(c, TNMC_ERR_ARG, "NULL argument");
+  if (!c->have_props) return fail(c, TNMC_ERR_STATE, "no proposals");
+  const int64_t n_cfg = (int64_t)c->n_real * c->n_chains * c->last_n;
+  cudaError_t e = tnmc::launch_unpack(c->packed, c->words, c->L * c->L, n_cfg, spins_dev, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "unpack");
+  ++c->launches;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_eval_conditionals(tnmc_ctx* c, int n, const int8_t* spins_dev, double* logq_dev,
+                                   double* qplus_dev) {
+  if (!c || !spins_dev) return fail(c, TNMC_ERR_ARG, "NULL argument");
+  if (!c->env_built) return fail(c, TNMC_ERR_STATE, "tnmc_eval_conditionals before tnmc_build_env");
+  if (n < 1) return fail(c, TNMC_ERR_ARG, "n must be >= 1");
+  if (!is_device_ptr(spins_dev)) return fail(c, TNMC_ERR_ARG, "spins_dev must be device memory");
+  double* lq = logq_dev;
+  double* tmp = nullptr;
+  if (!lq) {
+    if (cudaMalloc(&tmp, sizeof(double) * (size_t)c->n_real * n) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, TNMC_ERR_OOM, "log q buffer");
+    }
+    lq = tmp;
+  }
+  tnmc_status s = run_sample(c, n, 0, spins_dev, lq, qplus_dev, false);
+  if (tmp) { cudaStreamSynchronize(c->stream); cudaFree(tmp); }
+  return s;
+}
+
+tnmc_status tnmc_accept(tnmc_ctx* c, uint8_t* accepted_dev, int64_t* n_accepted_host) {
+  if (!c) return fail(nullptr, TNMC_ERR_ARG, "NULL context");
+  if (!c->have_props) return fail(c, TNMC_ERR_STATE, "tnmc_accept before tnmc_propose");
+  double before = 0.0;
+  std::vector<double> acc_h;
+  if (n_accepted_host) {
+    acc_h.resize((size_t)c->n_real * tnmc::ACC_SLOTS);
+    cudaError_t e = cudaMemcpyAsync(acc_h.data(), c->acc, acc_h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "accumulator read");
+    for (int k = 0; k < c->n_real; ++k) before += acc_h[(size_t)k * tnmc::ACC_SLOTS + tnmc::ACC_NACC];
+  }
+  tnmc::AcceptArgs a{};
+  a.L = c->L; a.n_real = c->n_real; a.n_chains = c->n_chains; a.n = c->last_n; a.words = c->words;
+  a.n_therm = c->n_therm; a.step0 = c->last_step0; a.beta = c->beta; a.seeds = c->seeds;
+  a.logq = c->logq; a.energy = c->energy; a.magnet = c->magnet; a.spins_packed = c->packed;
+  a.accepted = accepted_dev; a.have_state = c->have_state; a.cur_logq = c->cur_logq;
+  a.cur_energy = c->cur_energy; a.cur_magnet = c->cur_magnet; a.cur_spins = c->cur_spins;
+  a.acc = c->acc; a.cur_idx = c->cur_idx; a.status = c->status;
+  cudaError_t e = tnmc::launch_accept(a, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "accept launch");
+  ++c->launches;
+  c->have_props = false;
+  if (n_accepted_host) {
+    tnmc_status s = check_status(c);
+    if (s) return s;
+    e = cudaMemcpy(acc_h.data(), c->acc, acc_h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "accumulator read");
+    double after = 0.0;
+    for (int k = 0; k < c->n_real; ++k) after += acc_h[(size_t)k * tnmc::ACC_SLOTS + tnmc::ACC_NACC];
+    *n_accepted_host = (int64_t)llround(after - before);
+  }
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_observables(tnmc_ctx* c, tnmc_obs* out_host) {
+  if (!c || !out_host) return fail(c, TNMC_ERR_ARG, "NULL argument");
+  tnmc_status s = check_status(c);
+  if (s) return s;
+  std::vector<double> acc((size_t)c->n_real * tnmc::ACC_SLOTS);
+  std::vector<int64_t> cl(c->n_real);
+  cudaError_t e = cudaMemcpy(acc.data(), c->acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(cl.data(), c->clamps, cl.size() * sizeof(int64_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "observables copy");
+  for (int k = 0; k < c->n_real; ++k) {
+    const double* a = &acc[(size_t)k * tnmc::ACC_SLOTS];
+    tnmc_obs& o = out_host[k];
+    std::memset(&o, 0, sizeof(o));
+    o.n_prop = (int64_t)llround(a[tnmc::ACC_NPROP]);
+    o.n_acc = (int64_t)llround(a[tnmc::ACC_NACC]);
+    o.n_meas = (int64_t)llround(a[tnmc::ACC_NMEAS]);
+    o.n_meas_q = (int64_t)llround(a[tnmc::ACC_NMEASQ]);
+    o.clamps = cl[k];
+    const double nm = a[tnmc::ACC_NMEAS] > 0 ? a[tnmc::ACC_NMEAS] : 1.0;
+    const double nq = a[tnmc::ACC_NMEASQ] > 0 ? a[tnmc::ACC_NMEASQ] : 1.0;
+    o.E = a[tnmc::ACC_E] / nm; o.E2 = a[tnmc::ACC_E2] / nm; o.m_abs = a[tnmc::ACC_MABS] / nm;
+    o.m2 = a[tnmc::ACC_M2] / nm; o.m4 = a[tnmc::ACC_M4] / nm;
+    o.q = a[tnmc::ACC_Q] / nq; o.q_abs = a[tnmc::ACC_QABS] / nq; o.q2 = a[tnmc::ACC_Q2] / nq; o.q4 = a[tnmc::ACC_Q4] / nq;
+  }
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_reset_chains(tnmc_ctx* c) {
+  if (!c) return fail(nullptr, TNMC_ERR_ARG, "NULL context");
+  const size_t chains = (size_t)c->n_real * c->n_chains;
+  cudaError_t e = cudaMemsetAsync(c->have_state, 0, sizeof(int) * chains, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(double) * (size_t)c->n_real * tnmc::ACC_SLOTS, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->clamps, 0, sizeof(int64_t) * c->n_real, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reset");
+  c->have_props = false;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_destroy(tnmc_ctx* c) {
+  if (!c) return TNMC_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  delete c;
+  return TNMC_OK;
+}
+
+size_t tnmc_env_bytes(const tnmc_ctx* c) { return c ? c->env_bytes : 0; }
+
+tnmc_status tnmc_build_stats(tnmc_ctx* c, int64_t* out_host) {
+  if (!c || !out_host) return fail(c, TNMC_ERR_ARG, "NULL argument");
+  if (!c->env_built) return fail(c, TNMC_ERR_STATE, "no environments");
+  tnmc_status s = check_status(c);
+  if (s) return s;
+  std::vector<long long> st((size_t)4 * c->n_real);
+  cudaError_t e = cudaMemcpy(st.data(), c->stats, st.size() * sizeof(long long), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stats copy");
+  int64_t mx = 0, unc = 0, tot = 0, nsvd = 0;
+  for (int k = 0; k < c->n_real; ++k) {
+    mx = st[4 * k] > mx ? st[4 * k] : mx; unc += st[4 * k + 1]; tot += st[4 * k + 2]; nsvd += st[4 * k + 3];
+  }
+  out_host[0] = mx; out_host[1] = unc; out_host[2] = tot; out_host[3] = nsvd;
+  return TNMC_OK;
+}
+
+int64_t tnmc_launch_count(const tnmc_ctx* c) { return c ? c->launches : 0; }
+
+tnmc_status tnmc_copy_env(tnmc_ctx* c, int real, int row, double* tiles_host, int32_t* dims_host, double* lam_host) {
+  if (!c) return fail(nullptr, TNMC_ERR_ARG, "NULL context");
+  if (real < 0 || real >= c->n_real || row < 0 || row >= c->L) return fail(c, TNMC_ERR_ARG, "index out of range");
+  if (!c->env_built) return fail(c, TNMC_ERR_STATE, "no environments");
+  tnmc_status s = check_status(c);
+  if (s) return s;
+  const int L = c->L, CHI = c->CHI, chi = c->chi;
+  const size_t tile = (size_t)2 * CHI * CHI;
+  const size_t off = ((size_t)real * L + row) * L * tile;
+  std::vector<unsigned char> raw(L * tile * c->te_size);
+  cudaError_t e = cudaMemcpy(raw.data(), (const unsigned char*)c->env + off * c->te_size, raw.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "env copy");
+  if (tiles_host) {
+    for (int cc = 0; cc < L; ++cc)
+      for (int y = 0; y < 2; ++y)
+        for (int a = 0; a < chi; ++a)
+          for (int b = 0; b < chi; ++b) {
+            const size_t src = (size_t)cc * tile + (size_t)y * CHI * CHI + (size_t)a * CHI + b;
+            double v;
+            if (c->te_size == 8) { std::memcpy(&v, &raw[src * 8], 8); }
+            else if (c->te_size == 4) { float f; std::memcpy(&f, &raw[src * 4], 4); v = f; }
+            else { uint16_t h; std::memcpy(&h, &raw[src * 2], 2); uint32_t bits = (uint32_t)h << 16; float f; std::memcpy(&f, &bits, 4); v = f; }
+            tiles_host[(((size_t)cc * 2 + y) * chi + a) * chi + b] = v;
+          }
+  }
+  if (dims_host) {
+    e = cudaMemcpy(dims_host, c->kdim + ((size_t)real * L + row) * (L + 1), sizeof(int) * (L + 1), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dims copy");
+  }
+  if (lam_host) {
+    e = cudaMemcpy(lam_host, c->lam + (size_t)real * L + row, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lam copy");
+  }
+  return TNMC_OK;
+}
+
+}  // extern "C"
