@@ -179,6 +179,37 @@ tnmc_status tnmc_copy_env(tnmc_ctx* ctx, int real, int row, double* tiles_host,
  * [2] = total sweeps, [3] = truncating SVDs performed.  Synchronises. */
 tnmc_status tnmc_build_stats(tnmc_ctx* ctx, int64_t* out_host);
 
+/* Environment build that allocates nothing.  The paper has no counterpart: this is a
+ * service for callers that cannot call cudaMalloc -- an application that reserves all
+ * device memory up front and forbids allocation afterwards, or a latency-critical path where
+ * cudaMalloc's device-wide synchronisation is not allowed.
+ * It runs the same boundary-MPS build as tnmc_build_env for n_real realizations, reading and
+ * writing only the caller's buffers plus one file-scope device array of 32 MiB that every GPU
+ * which loads the library holds until the process exits (the R factors, working rows,
+ * bond-dimension array, statistics and status word live there).
+ *   couplings_dev: device, n_real * 2L(L-1) int8 +-1 in the layout above (not validated);
+ *   beta_dev     : device, n_real doubles;
+ *   precision    : tnmc_precision (the build runs in FP64 for TNMC_FP64, FP32 otherwise);
+ *   env_dev      : device output, n_real * L * L tiles of 2*C*C elements ([real][row][site]
+ *                  [y][alpha][beta], zero padded), C the smallest of 4, 8, 16, 32 that is
+ *                  >= chi; elements are double (FP64), bfloat16 (MIXED_BF16) or float;
+ *   kdim_dev     : device output, n_real * L * (L+1) int32 bond dimensions;
+ *   lam_dev      : device output, n_real * L row log-norms; logz_dev: n_real log Z;
+ *   stream       : cudaStream_t (NULL = default stream); the call only queues work.
+ * The first call on a device looks up the device address of the array (once per device,
+ * with that device current); make that first call before any stream capture.  Every call
+ * shares the one array and leaves the last call's contents in it (the status word is cleared
+ * at the start of each call): calls whose work overlaps on the GPU race and corrupt each
+ * other, so serialise them (one stream, or events).
+ * Errors: TNMC_ERR_ARG for bad sizes or NULL buffers, and when the scratch this build needs,
+ * n_real * ((2*L*2*C*C + L*4*C*C) * w + 4*(L+1)) bytes plus alignment (w = 8 for FP64, 4
+ * otherwise), exceeds the 32 MiB array; TNMC_ERR_UNSUPPORTED for chi > 32; TNMC_ERR_CUDA
+ * for a failed launch.  Device-side status is not returned (no synchronisation). */
+tnmc_status tnmc_build_env_noalloc(int L, int n_real, int chi, int precision,
+                                   const int8_t* couplings_dev, const double* beta_dev,
+                                   void* env_dev, int32_t* kdim_dev, double* lam_dev,
+                                   double* logz_dev, void* stream);
+
 /* Kernel launch accounting: number of kernels this context launched since creation. */
 int64_t tnmc_launch_count(const tnmc_ctx* ctx);
 

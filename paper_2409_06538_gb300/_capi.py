@@ -36,6 +36,8 @@ SIGNATURES = {
     "tnmc_copy_env": (c_int, [c_void_p, c_int, c_int, c_double_p, c_int32_p, c_double_p]),
     "tnmc_launch_count": (c_int64, [c_void_p]),
     "tnmc_build_stats": (c_int, [c_void_p, c_int64_p]),
+    "tnmc_build_env_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_void_p, c_void_p, c_void_p]),
 }
 
 
