@@ -33,18 +33,108 @@ template <typename T, int D> __device__ __forceinline__ T jacobi_tol() {
   return T(4) * num<T>::sqrt_(T(D)) * num<T>::eps;
 }
 
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+__device__ __forceinline__ float dot16(const float4& a, const float4& b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+__device__ __forceinline__ double dot16(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
+__device__ __forceinline__ void rot16(float4& u, float4& v, float c, float s) {
+  const float4 a = u, b = v;
+  u = make_float4(c * a.x - s * b.x, c * a.y - s * b.y, c * a.z - s * b.z, c * a.w - s * b.w);
+  v = make_float4(s * a.x + c * b.x, s * a.y + c * b.y, s * a.z + c * b.z, s * a.w + c * b.w);
+}
+__device__ __forceinline__ void rot16(double2& u, double2& v, double c, double s) {
+  const double2 a = u, b = v;
+  u = make_double2(c * a.x - s * b.x, c * a.y - s * b.y);
+  v = make_double2(s * a.x + c * b.x, s * a.y + c * b.y);
+}
+// Jacobi rotation (c, s) that makes columns p, q orthogonal, from a = |y_p|^2, b = |y_q|^2,
+// g = y_p . y_q (y_p' = c y_p - s y_q, y_q' = s y_p + c y_q).  The angle solves
+// tan 2theta = 2g / (b - a) with |theta| <= pi/4:
+//   r = sqrt((b-a)^2 + 4 g^2), cos 2theta = |b-a| / r, c = sqrt((1 + cos 2theta) / 2),
+//   s = sgn(b-a) g / (r c)   (sgn(0) = +1),
+// two reciprocal square roots in sequence instead of the divide/sqrt chain of the tangent
+// form.  FP32 uses the hardware rsqrt with one Newton step each, so c^2 + s^2 = 1 to
+// working precision; FP64 uses IEEE operations.
+__device__ __forceinline__ float rsqrt_nr(float x) {
+  const float r = rsqrtf(x);
+  return r * fmaf(-0.5f * x * r, r, 1.5f);
+}
+__device__ __forceinline__ void rotation_from_gram(double a, double b, double g, double& c, double& s) {
+  const double d = b - a;
+  const double rinv = 1.0 / sqrt(d * d + 4.0 * g * g);
+  const double h = 0.5 + 0.5 * fabs(d) * rinv;
+  const double ic = 1.0 / sqrt(h);
+  c = h * ic;
+  s = (d < 0.0 ? -g : g) * rinv * ic;
+}
+__device__ __forceinline__ void rotation_from_gram(float a, float b, float g, float& c, float& s) {
+  const float d = b - a;
+  const float rinv = rsqrt_nr(fmaf(d, d, 4.0f * g * g));
+  const float h = fmaf(0.5f * fabsf(d), rinv, 0.5f);
+  const float ic = rsqrt_nr(h);
+  c = h * ic;
+  s = (d < 0.0f ? -g : g) * rinv * ic;
+}
+
+template <typename T> __device__ __forceinline__ T group8_sum(T v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  return v;
+}
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// 4-element shared-memory vectors (16 B for float, 2 x 16 B for double); callers keep the
+// index a multiple of 4 so the accesses are aligned.
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4]) { *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]); }
+__device__ __forceinline__ void st4(double* p, const double v[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void cp_async16_env(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit_env() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_env() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// Copy `bytes` (a multiple of 16) from global to shared memory with cp.async (no wait).
+__device__ __forceinline__ void prefetch_async(void* smem, const void* gmem, int bytes, int tid, int nt) {
+  for (int i = tid; i < bytes / 16; i += nt)
+    cp_async16_env(static_cast<char*>(smem) + 16 * i, static_cast<const char*>(gmem) + 16 * i);
+  cp_async_commit_env();
+}
+
 template <int CHI> struct EnvCfg {
   static constexpr int D = 2 * CHI;                 // MPO bond x MPS bond
-  static constexpr int NWARP = CHI < 4 ? 4 : CHI;   // one warp per Jacobi pair
+  static constexpr int NWARP = CHI < 4 ? 4 : (CHI > 16 ? 16 : CHI);   // >= 8*CHI/32 Jacobi lanes
   static constexpr int NT = 32 * NWARP;
   static constexpr int TILE = 2 * CHI * CHI;        // [y][alpha][beta]
 };
 
+// Column stride of Y and V: at least 8 lanes x 16 bytes, so that the 8 lanes of a Jacobi
+// pair read one contiguous 128-byte segment per vector load (no bank conflicts).
+template <typename T, int CHI> struct JStride {
+  static constexpr int D = 2 * CHI;
+  static constexpr int VEC = 16 / (int)sizeof(T);
+  static constexpr int DP = D > 8 * VEC ? D : 8 * VEC;
+};
+
 template <typename T, int CHI>
 __host__ __device__ constexpr size_t env_smem_elems() {
-  // backward: M, Y, V, R (D*D each) + P (D*CHI) + Q (2*CHI*CHI) + tile (2*CHI*CHI)
-  // forward : X (2D*D) + R (D*D) + tile -- the union is the backward footprint
-  return (size_t)4 * (2 * CHI) * (2 * CHI) + (size_t)(2 * CHI) * CHI + 2 * (size_t)2 * CHI * CHI;
+  // backward: M, R (D*D each), Y, V (D*DP each) + P (D*CHI) + Q (2*CHI*CHI) + tile (2*CHI*CHI)
+  // forward : X (2D*D, aliases M and Y) + R (D*D) + tile
+  return (size_t)2 * (2 * CHI) * (2 * CHI) + (size_t)2 * (2 * CHI) * JStride<T, CHI>::DP +
+         (size_t)(2 * CHI) * CHI + 2 * (size_t)2 * CHI * CHI;
 }
 
 template <int CHI> struct Pair {
@@ -70,10 +160,11 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   // backward-phase layout
+  constexpr int DP = JStride<T, CHI>::DP;
   T* Mc = sm;                 // D x D   col-major, compact columns j = x*kn + g
-  T* Yc = Mc + D * D;         // D x D   col-major
-  T* Vc = Yc + D * D;         // D x D   col-major (rows < n)
-  T* Rc = Vc + D * D;         // D x D   col-major R_c
+  T* Yc = Mc + D * D;         // n columns of stride DP (rows >= D zero)
+  T* Vc = Yc + D * DP;        // n columns of stride DP (rows >= n zero)
+  T* Rc = Vc + D * DP;        // D x D   col-major R_c
   T* Ps = Rc + D * D;         // D x CHI col-major: P[(b,be)][g] at g*D + b*CHI + be
   T* Qs = Ps + D * CHI;       // 2 x CHI x CHI: Q[b][al][g]
   T* Bt = Qs + TILE;          // previous-row tile [y][al][be]
@@ -81,6 +172,9 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
   T* Xs = sm;                 // 2D x D col-major
 
   __shared__ T Wc[8];               // W[x][a][b] at x*4 + a*2 + b
+  int8_t* jv_s = reinterpret_cast<int8_t*>(Bt + TILE);        // Jv[r][c], L entries
+  int8_t* jh_s = jv_s + args.L;                                // Jh[r+1][c], L-1 entries
+  const T eb = (T)exp(beta), ebm = (T)exp(-beta);             // exp(+-beta): every Boltzmann weight
   __shared__ T vbuf[2][2 * D];      // Householder vectors (double-buffered)
   __shared__ T vcoef[2];
   __shared__ T red[32];
@@ -129,58 +223,100 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       dqr[0] = 1;
       for (int c = 0; c < L - 1; ++c) dqr[c + 1] = min(2 * dqr[c], 2 * kold[c + 1]);
     }
+    for (int c = tid; c < L; c += NT) jv_s[c] = Jv[(size_t)r * L + c];
+    for (int c = tid; c < L - 1; c += NT) jh_s[c] = Jh[(size_t)(r + 1) * (L - 1) + c];
+    // W(x,a,b) of site c from exp(+-beta): the vertical bond to the row below and the
+    // horizontal bond of the row below (absent at c = 0, where only a = 0 exists)
+    auto set_w = [&](int c) {
+      if (tid < 8) {
+        const int x = tid >> 2, a = (tid >> 1) & 1, b = tid & 1;
+        T w = (jv_s[c] * spin_of(x) * spin_of(b) > 0) ? eb : ebm;
+        if (c > 0) w *= (jh_s[c - 1] * spin_of(a) * spin_of(b) > 0) ? eb : ebm;
+        else if (a == 1) w = T(0);
+        Wc[tid] = w;
+      }
+    };
     // R_0 = [1]
     for (int e = tid; e < D * D; e += NT) Rc[e] = (e == 0) ? T(1) : T(0);
     if (tid == 0) {
       for (int e = 0; e < D * D; ++e) Rstore[e] = (e == 0) ? T(1) : T(0);
     }
+    prefetch_async(Bt, prev, TILE * (int)sizeof(T), tid, NT);      // tile of site 0
     __syncthreads();
 
     // ---------------- forward sweep: R factors of the left parts ----------------
     for (int c = 0; c < L - 1; ++c) {
-      const T* btile = prev + (size_t)c * TILE;
-      for (int e = tid; e < TILE; e += NT) Bt[e] = btile[e];
-      if (tid < 8) {
-        const int x = tid >> 2, a = (tid >> 1) & 1, b = tid & 1;
-        double w = exp(beta * (double)Jv[(size_t)r * L + c] * spin_of(x) * spin_of(b));
-        if (c > 0) w *= exp(beta * (double)Jh[(size_t)(r + 1) * (L - 1) + c - 1] * spin_of(a) * spin_of(b));
-        else if (a == 1) w = 0.0;
-        Wc[tid] = (T)w;
-      }
+      set_w(c);
+      cp_async_wait_env();
       __syncthreads();
-      // X[(x,i),(b,be)] = sum_al (W(x,0,b) R[i][al] + W(x,1,b) R[i][CHI+al]) B[b][al][be]
-      for (int e = tid; e < 2 * D * D; e += NT) {
-        const int row = e % (2 * D), col = e / (2 * D);
-        const int x = row / D, i = row % D, b = col / CHI, be = col % CHI;
+      // X[(x,i),(b,be)] = sum_al (W(x,0,b) R[i][al] + W(x,1,b) R[i][CHI+al]) B[b][al][be]:
+      // four (D x CHI) = (D x CHI)(CHI x CHI) products, 4 x 4 register tiles
+      constexpr int TI = D / 4, TB = CHI / 4;
+      for (int u = tid; u < 4 * TI * TB; u += NT) {
+        const int xb = u / (TI * TB), rem = u % (TI * TB);
+        const int x = xb >> 1, b = xb & 1, i0 = (rem % TI) * 4, b0 = (rem / TI) * 4;
         const T w0 = Wc[x * 4 + 0 * 2 + b], w1 = Wc[x * 4 + 1 * 2 + b];
-        const T* bb = Bt + b * CHI * CHI + be;
-        T acc = 0;
-#pragma unroll 8
-        for (int al = 0; al < CHI; ++al)
-          acc += (w0 * Rc[al * D + i] + w1 * Rc[(CHI + al) * D + i]) * bb[al * CHI];
-        Xs[e] = acc;
+        T acc[4][4] = {};
+#pragma unroll 4
+        for (int al = 0; al < CHI; ++al) {
+          T r0[4], r1[4], bv[4];
+          ld4(Rc + al * D + i0, r0);
+          ld4(Rc + (CHI + al) * D + i0, r1);
+          ld4(Bt + b * CHI * CHI + al * CHI + b0, bv);
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) {
+            const T rw = w0 * r0[ii] + w1 * r1[ii];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) acc[ii][jj] += rw * bv[jj];
+          }
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const T col4[4] = {acc[0][jj], acc[1][jj], acc[2][jj], acc[3][jj]};
+          st4(Xs + (size_t)(b * CHI + b0 + jj) * (2 * D) + x * D + i0, col4);
+        }
       }
       __syncthreads();
+      // the next site's tile streams in while the QR runs
+      prefetch_async(Bt, prev + (size_t)(c + 1) * TILE, TILE * (int)sizeof(T), tid, NT);
       // Householder QR of X (m = 2D rows, D columns); warp (j % NWARP) owns column j.
       constexpr int m = 2 * D;
       const T tiny = (sizeof(T) == 4) ? T(1e-36) : T(1e-300);
+      // Each lane owns rows lane + 32 t (t < m/32) of a column; the reflector vector is
+      // stored zero above its pivot row, so the updates run over all rows unconditionally.
+      constexpr int RPL = m / 32 > 0 ? m / 32 : 1;     // rows per lane
       auto house = [&](int j) {   // executed by the owning warp for column j
         T* col = Xs + (size_t)j * m;
+        T xr[RPL];
         T ss = 0;
-        for (int i = j + lane; i < m; i += 32) ss += col[i] * col[i];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          const int i = lane + 32 * t;
+          xr[t] = (i < m && i >= j) ? col[i] : T(0);
+          ss += xr[t] * xr[t];
+        }
         ss = warp_sum(ss);
         const T x0 = col[j];
-        __syncwarp();
+        __syncwarp();                 // every lane has read the pivot before any lane writes
         if (ss <= tiny) {
-          for (int i = j + 1 + lane; i < m; i += 32) col[i] = T(0);
+#pragma unroll
+          for (int t = 0; t < RPL; ++t) {
+            const int i = lane + 32 * t;
+            if (i < m) { vbuf[j & 1][i] = T(0); if (i > j) col[i] = T(0); }
+          }
           if (lane == 0) vcoef[j & 1] = T(0);
         } else {
           const T nrm = num<T>::sqrt_(ss);
           const T alpha = x0 >= T(0) ? -nrm : nrm;
           const T v0 = x0 - alpha;
-          for (int i = j + lane; i < m; i += 32) vbuf[j & 1][i] = (i == j) ? v0 : col[i];
-          __syncwarp();
-          for (int i = j + lane; i < m; i += 32) col[i] = (i == j) ? alpha : T(0);
+#pragma unroll
+          for (int t = 0; t < RPL; ++t) {
+            const int i = lane + 32 * t;
+            if (i < m) {
+              vbuf[j & 1][i] = (i == j) ? v0 : xr[t];
+              if (i >= j) col[i] = (i == j) ? alpha : T(0);
+            }
+          }
           if (lane == 0) vcoef[j & 1] = T(1) / (nrm * (nrm + (x0 >= T(0) ? x0 : -x0)));  // 2/|v|^2
         }
       };
@@ -188,18 +324,39 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       for (int j = 0; j < D; ++j) {
         __syncthreads();
         const T coef = vcoef[j & 1];
-        if (coef != T(0)) {
-          const T* v = vbuf[j & 1];
-          for (int k = j + 1 + ((warp - (j + 1)) % NWARP + NWARP) % NWARP; k < D; k += NWARP) {
-            T* col = Xs + (size_t)k * m;
-            T d = 0;
-            for (int i = j + lane; i < m; i += 32) d += v[i] * col[i];
-            d = warp_sum(d) * coef;
-            for (int i = j + lane; i < m; i += 32) col[i] -= d * v[i];
+        const T* v = vbuf[j & 1];
+        auto apply = [&](int k) {
+          T* col = Xs + (size_t)k * m;
+          T xr[RPL], vr[RPL];
+          T d = 0;
+#pragma unroll
+          for (int t = 0; t < RPL; ++t) {
+            const int i = lane + 32 * t;
+            xr[t] = i < m ? col[i] : T(0);
+            vr[t] = i < m ? v[i] : T(0);
+            d += vr[t] * xr[t];
           }
+          d = warp_sum(d) * coef;
+#pragma unroll
+          for (int t = 0; t < RPL; ++t) {
+            const int i = lane + 32 * t;
+            if (i < m) col[i] = xr[t] - d * vr[t];
+          }
+        };
+        // the owner of column j+1 updates it first and forms the next reflector at once;
+        // every other column of this warp is updated afterwards (needed only later)
+        const int nxt = j + 1;
+        const bool owner = nxt < D && warp == nxt % NWARP;
+        if (owner) {
+          if (coef != T(0)) apply(nxt);
+          __syncwarp();
+          house(nxt);
+        }
+        if (coef != T(0)) {
+          for (int k = j + 1 + ((warp - (j + 1)) % NWARP + NWARP) % NWARP; k < D; k += NWARP)
+            if (!(owner && k == nxt)) apply(k);
         }
         __syncwarp();
-        if (j + 1 < D && warp == (j + 1) % NWARP) house(j + 1);
       }
       __syncthreads();
       // scale: max |R_jj|; R_{c+1} = X[0:D, :] / scale (col-major), also to Rstore[c+1]
@@ -232,27 +389,41 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
     if (tid == 0) knew[L] = 1;
     __syncthreads();
     for (int c = L - 1; c >= 0; --c) {
-      const T* btile = prev + (size_t)c * TILE;
-      for (int e = tid; e < TILE; e += NT) Bt[e] = btile[e];
-      if (tid < 8) {
-        const int x = tid >> 2, a = (tid >> 1) & 1, b = tid & 1;
-        double w = exp(beta * (double)Jv[(size_t)r * L + c] * spin_of(x) * spin_of(b));
-        if (c > 0) w *= exp(beta * (double)Jh[(size_t)(r + 1) * (L - 1) + c - 1] * spin_of(a) * spin_of(b));
-        else if (a == 1) w = 0.0;
-        Wc[tid] = (T)w;
-      }
+      // Bt (tile c) and Rc (R_c) were prefetched during the previous site
+      set_w(c);
+      cp_async_wait_env();
       __syncthreads();
-      // Q[b][al][g] = sum_be B[b][al][be] P[(b,be)][g]
-      for (int e = tid; e < TILE; e += NT) {
-        const int b = e / (CHI * CHI), al = (e / CHI) % CHI, g = e % CHI;
-        T acc = 0;
-        if (g < kn) {
-#pragma unroll 8
-          for (int be = 0; be < CHI; ++be) acc += Bt[b * CHI * CHI + al * CHI + be] * Ps[g * D + b * CHI + be];
+      // Q[b][al][g] = sum_be B[b][al][be] P[(b,be)][g]: 4 x 4 register tiles
+      {
+        constexpr int TA = CHI / 4;
+        for (int u = tid; u < 2 * TA * TA; u += NT) {
+          const int b = u / (TA * TA), a0 = ((u % (TA * TA)) % TA) * 4, g0 = ((u % (TA * TA)) / TA) * 4;
+          T acc[4][4] = {};
+          if (g0 < kn) {
+#pragma unroll 4
+            for (int be = 0; be < CHI; ++be) {
+              T bv[4], pv[4];
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii) bv[ii] = Bt[b * CHI * CHI + (a0 + ii) * CHI + be];
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) pv[jj] = Ps[(g0 + jj) * D + b * CHI + be];
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] += bv[ii] * pv[jj];
+            }
+          }
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) {
+            T row4[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) row4[jj] = (g0 + jj < kn) ? acc[ii][jj] : T(0);
+            st4(Qs + b * CHI * CHI + (a0 + ii) * CHI + g0, row4);
+          }
         }
-        Qs[e] = acc;
       }
       __syncthreads();
+      if (c > 0) prefetch_async(Bt, prev + (size_t)(c - 1) * TILE, TILE * (int)sizeof(T), tid, NT);
       const int n = 2 * kn;    // compact columns j = x*kn + g
       // M[(a,al)][j] = sum_b W(x,a,b) Q[b][al][g]
       for (int e = tid; e < D * n; e += NT) {
@@ -283,20 +454,42 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
         __syncthreads();
         break;
       }
-      // Y = R_c M  (D x n); the R factor of the left part up to site c-1
-      const T* Rin = Rstore + (size_t)c * D * D;
-      for (int e = tid; e < D * D; e += NT) Rc[e] = Rin[e];
-      __syncthreads();
+      // Y = R_c M  (D x n; R_c, the R factor of the left part up to site c-1, was
+      // prefetched): 4 x 4 register tiles over (rows, compact columns)
       T fro = 0;
-      for (int e = tid; e < D * n; e += NT) {
-        const int i = e % D, j = e / D;
-        T acc = 0;
-#pragma unroll 8
-        for (int l = 0; l < D; ++l) acc += Rc[l * D + i] * Mc[(size_t)j * D + l];
-        Yc[e] = acc;
-        fro += acc * acc;
+      {
+        constexpr int TI = D / 4;
+        const int TJ = (n + 3) / 4;
+        for (int u = tid; u < TI * TJ; u += NT) {
+          const int i0 = (u % TI) * 4, j0 = (u / TI) * 4;
+          T acc[4][4] = {};
+#pragma unroll 4
+          for (int l = 0; l < D; ++l) {
+            T rv[4], mv[4];
+            ld4(Rc + l * D + i0, rv);
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) mv[jj] = (j0 + jj < n) ? Mc[(size_t)(j0 + jj) * D + l] : T(0);
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) acc[ii][jj] += rv[ii] * mv[jj];
+          }
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            if (j0 + jj < n) {
+              const T col4[4] = {acc[0][jj], acc[1][jj], acc[2][jj], acc[3][jj]};
+              st4(Yc + (size_t)(j0 + jj) * DP + i0, col4);
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii) fro += acc[ii][jj] * acc[ii][jj];
+            }
+          }
+        }
+        if constexpr (DP > D) {
+          constexpr int PAD = DP > D ? DP - D : 1;
+          for (int e = tid; e < PAD * n; e += NT) Yc[(size_t)(e / PAD) * DP + D + e % PAD] = T(0);
+        }
       }
-      for (int e = tid; e < D * n; e += NT) { const int i = e % D, j = e / D; Vc[e] = (i == j) ? T(1) : T(0); }
+      for (int e = tid; e < DP * n; e += NT) { const int i = e % DP, j = e / DP; Vc[e] = (i == j) ? T(1) : T(0); }
       fro = warp_sum(fro);
       if (lane == 0) red[warp] = fro;
       if (tid == 0) { rot[0] = 0; rot[1] = 0; }
@@ -308,46 +501,73 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       }
       __syncthreads();
       const T tinyY = red[NWARP] * num<T>::eps * num<T>::eps;
+      // R_{c-1} streams in while the SVD runs (Rc is not read again at this site)
+      if (c > 1) prefetch_async(Rc, Rstore + (size_t)(c - 1) * D * D, D * D * (int)sizeof(T), tid, NT);
       const T tol = jacobi_tol<T, D>();
+      // One-sided Jacobi: the n/2 pairs of a round are disjoint; 8 lanes per pair, each lane
+      // holding DP/8 rows of both columns in 16-byte vectors; the three dot products of a
+      // pair are reduced together over the 8 lanes.
+      constexpr int NJ = 8 * CHI;
+      constexpr int VEC = JStride<T, CHI>::VEC;
+      constexpr int NV = DP / (8 * VEC);
+      using V16 = typename Vec16<T>::type;
       int sweep = 0;
-      for (; sweep < JacobiTol<T>::maxsw; ++sweep) {
-        if (tid == 0) rot[(sweep + 1) & 1] = 0;
-        for (int rd = 0; rd < n - 1; ++rd) {
-          if (warp < n / 2) {
-            int p, q;
-            Pair<CHI>::get(n, rd, warp, p, q);
-            T* yp = Yc + (size_t)p * D;
-            T* yq = Yc + (size_t)q * D;
-            T a = 0, b = 0, g = 0;
-#pragma unroll
-            for (int t = 0; t < D / 32 + (D % 32 ? 1 : 0); ++t) {
-              const int i = lane + 32 * t;
-              if (i < D) { const T u = yp[i], v = yq[i]; a += u * u; b += v * v; g += u * v; }
+      if (tid < NJ) {
+        const int w = tid >> 3, li = tid & 7;
+        const bool active = w < n / 2;
+        const int m1 = n - 1;
+        for (; sweep < JacobiTol<T>::maxsw; ++sweep) {
+          if (tid == 0) rot[(sweep + 1) & 1] = 0;
+          // round-robin pair of slot w in round 0; each later round adds 1 (mod n-1) to
+          // both members, except that slot 0 keeps column n-1
+          int p = 0, q = 0;
+          if (active) Pair<CHI>::get(n, 0, w, p, q);
+          for (int rd = 0; rd < m1; ++rd) {
+            if (rd > 0 && active) {
+              if (w != 0) p = (p + 1 == m1) ? 0 : p + 1;
+              q = (q + 1 == m1) ? 0 : q + 1;
             }
-            a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
-            const T ag = g < T(0) ? -g : g;
-            if (a > tinyY && b > tinyY && ag > tol * num<T>::sqrt_(a) * num<T>::sqrt_(b)) {
-              const T z = (b - a) / (T(2) * g);
-              const T az = z < T(0) ? -z : z;
-              T t = (az > T(1e15)) ? T(0.5) / az : T(1) / (az + num<T>::sqrt_(T(1) + z * z));
-              if (z < T(0)) t = -t;
-              const T cs = T(1) / num<T>::sqrt_(T(1) + t * t), sn = cs * t;
+            V16* yp = reinterpret_cast<V16*>(Yc + (size_t)p * DP);
+            V16* yq = reinterpret_cast<V16*>(Yc + (size_t)q * DP);
+            V16* vp = reinterpret_cast<V16*>(Vc + (size_t)p * DP);
+            V16* vq = reinterpret_cast<V16*>(Vc + (size_t)q * DP);
+            V16 up[NV], uq[NV], wp[NV], wq[NV];
+            T g = 0, a = 0, b = 0;
 #pragma unroll
-              for (int tt = 0; tt < D / 32 + (D % 32 ? 1 : 0); ++tt) {
-                const int i = lane + 32 * tt;
-                if (i < D) { const T u = yp[i], v = yq[i]; yp[i] = cs * u - sn * v; yq[i] = sn * u + cs * v; }
-                if (i < n) {
-                  T* vp = Vc + (size_t)p * D; T* vq = Vc + (size_t)q * D;
-                  const T u = vp[i], v = vq[i]; vp[i] = cs * u - sn * v; vq[i] = sn * u + cs * v;
-                }
+            for (int k = 0; k < NV; ++k) {
+              up[k] = yp[li + 8 * k];
+              uq[k] = yq[li + 8 * k];
+              wp[k] = vp[li + 8 * k];     // issued early: their latency overlaps the reductions
+              wq[k] = vq[li + 8 * k];
+            }
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+              g += dot16(up[k], uq[k]);
+              a += dot16(up[k], up[k]);
+              b += dot16(uq[k], uq[k]);
+            }
+            g = group8_sum(g); a = group8_sum(a); b = group8_sum(b);
+            const bool do_rot = active && a > tinyY && b > tinyY && g * g > tol * tol * a * b;
+            if (do_rot) {
+              T cs, sn;
+              rotation_from_gram(a, b, g, cs, sn);
+#pragma unroll
+              for (int k = 0; k < NV; ++k) {
+                rot16(up[k], uq[k], cs, sn);
+                rot16(wp[k], wq[k], cs, sn);
+                yp[li + 8 * k] = up[k];
+                yq[li + 8 * k] = uq[k];
+                vp[li + 8 * k] = wp[k];
+                vq[li + 8 * k] = wq[k];
               }
-              if (lane == 0) rot[sweep & 1] = 1;
+              if (li == 0) rot[sweep & 1] = 1;
             }
+            named_barrier(1, NJ);
           }
-          __syncthreads();
+          if (rot[sweep & 1] == 0) break;
         }
-        if (rot[sweep & 1] == 0) break;
       }
+      __syncthreads();
       if (sweep + 1 > max_sweeps_seen) max_sweeps_seen = sweep + 1;
       if (sweep >= JacobiTol<T>::maxsw) ++unconverged;
       total_sweeps += (long long)min(sweep + 1, JacobiTol<T>::maxsw);
@@ -355,7 +575,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       // singular values = column norms of the rotated Y
       for (int j = warp; j < n; j += NWARP) {
         T ss = 0;
-        for (int i = lane; i < D; i += 32) ss += Yc[(size_t)j * D + i] * Yc[(size_t)j * D + i];
+        for (int i = lane; i < D; i += 32) ss += Yc[(size_t)j * DP + i] * Yc[(size_t)j * DP + i];
         ss = warp_sum(ss);
         if (lane == 0) sig[j] = ss;
       }
@@ -375,22 +595,41 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       for (int e = tid; e < TILE; e += NT) {
         const int y = e / (CHI * CHI), al = (e / CHI) % CHI, be = e % CHI;
         T v = T(0);
-        if (al < k && be < kn) v = Vc[(size_t)sel[al] * D + y * kn + be];
+        if (al < k && be < kn) v = Vc[(size_t)sel[al] * DP + y * kn + be];
         ctile[e] = v;
         etile[e] = env_store<TE, T>(v);
       }
-      // P[(a,al)][g] = sum_j M[(a,al)][j] V[j][sel[g]]
+      // P[(a,al)][g] = sum_j M[(a,al)][j] V[j][sel[g]]: 4 x 4 register tiles
       T pmax = 0;
-      for (int e = tid; e < D * CHI; e += NT) {
-        const int row = e % D, g = e / D;
-        T acc = 0;
-        if (g < k) {
-          const T* vcol = Vc + (size_t)sel[g] * D;
-          for (int j = 0; j < n; ++j) acc += Mc[(size_t)j * D + row] * vcol[j];
+      {
+        constexpr int TI = D / 4, TG = CHI / 4;
+        for (int u = tid; u < TI * TG; u += NT) {
+          const int i0 = (u % TI) * 4, g0 = (u / TI) * 4;
+          T acc[4][4] = {};
+          if (g0 < k) {
+            const T* vc[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) vc[jj] = Vc + (size_t)sel[(g0 + jj < k) ? g0 + jj : g0] * DP;
+#pragma unroll 4
+            for (int j = 0; j < n; ++j) {
+              T mv[4], vv[4];
+              ld4(Mc + (size_t)j * D + i0, mv);
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) vv[jj] = (g0 + jj < k) ? vc[jj][j] : T(0);
+#pragma unroll
+              for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] += mv[ii] * vv[jj];
+            }
+          }
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const T col4[4] = {acc[0][jj], acc[1][jj], acc[2][jj], acc[3][jj]};
+            st4(Ps + (size_t)(g0 + jj) * D + i0, col4);
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) { const T aa = acc[ii][jj] < T(0) ? -acc[ii][jj] : acc[ii][jj]; pmax = aa > pmax ? aa : pmax; }
+          }
         }
-        Ps[e] = acc;
-        const T aa = acc < T(0) ? -acc : acc;
-        pmax = aa > pmax ? aa : pmax;
       }
       pmax = warp_max(pmax);
       if (lane == 0) red[warp] = pmax;
@@ -454,7 +693,8 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
 template <typename T, typename TE, int CHI>
 cudaError_t launch_env_build_t(const EnvBuildArgs<T, TE>& a, cudaStream_t st) {
   using C = EnvCfg<CHI>;
-  const size_t smem = env_smem_elems<T, CHI>() * sizeof(T);
+  // + the two rows' couplings (int8) staged behind the tile
+  const size_t smem = env_smem_elems<T, CHI>() * sizeof(T) + (size_t)2 * a.L + 16;
   cudaError_t e = cudaFuncSetAttribute(env_build_kernel<T, TE, CHI>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
