@@ -33,7 +33,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["bf16", "tf32", "fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32", choices=["bf16", "tf32", "fp32", "fp64"])
     ap.add_argument("--L", type=int, default=256)
     ap.add_argument("--chi", type=int, default=32)
     ap.add_argument("--R", type=int, default=64, help="realizations per GPU")

@@ -36,6 +36,7 @@ struct tnmc_ctx {
   unsigned* status = nullptr;
   // sampling
   void* work = nullptr;
+  void* work_tc = nullptr;        // workspace of the tensor-core sampler (mixed TF32 path)
   uint32_t* packed = nullptr;
   double* logq = nullptr;
   int32_t* energy = nullptr;
@@ -207,6 +208,8 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
   TRY(dalloc(c, &c->stats, sizeof(long long) * 4 * n_real));
   TRY(dalloc(c, &c->status, sizeof(unsigned)));
   TRY(dalloc(c, &c->work, tnmc::sample_work_bytes(L, CHI, c->precision, c->num_sms)));
+  if (c->precision == TNMC_MIXED_TF32 && tnmc::sample_tc_supported(CHI))
+    TRY(dalloc(c, &c->work_tc, tnmc::sample_tc_work_bytes(L, CHI, c->num_sms)));
   TRY(dalloc(c, &c->clamps, sizeof(int64_t) * n_real));
   const size_t chains = (size_t)n_real * c->n_chains;
   TRY(dalloc(c, &c->have_state, sizeof(int) * chains));
@@ -295,7 +298,13 @@ static tnmc_status run_sample(tnmc_ctx* c, int n, uint64_t step0, const int8_t* 
   a.logq = logq; a.energy = props ? c->energy : nullptr; a.magnet = props ? c->magnet : nullptr;
   a.clamps = props ? c->clamps : nullptr; a.forced = forced; a.qplus = qplus; a.work = c->work;
   a.status = c->status;
-  cudaError_t e = tnmc::launch_sample(a, c->precision, c->CHI, c->num_sms, c->stream);
+  cudaError_t e;
+  if (c->work_tc) {
+    a.work = c->work_tc;
+    e = tnmc::launch_sample_tc(a, c->CHI, c->num_sms, c->stream);
+  } else {
+    e = tnmc::launch_sample(a, c->precision, c->CHI, c->num_sms, c->stream);
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "sample launch");
   ++c->launches;
   return TNMC_OK;

@@ -1,6 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the oracle, element by element on the
 same seeded inputs (spin draws, conditionals, log q, energies, accept decisions,
-observables) for the FP64, FP32 and BF16 paths."""
+observables) for the FP64, FP32 and mixed TF32 (tensor-core) paths, and the measured
+error of BF16-stored environments."""
 import numpy as np
 import pytest
 
@@ -35,7 +36,7 @@ def test_couplings_bit_exact(tn):
             assert np.array_equal(J[k], lattice.couplings_pmj(s, L, 0.109))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32"])
 def test_exact_when_untruncated(tn, precision):
     """chi >= 2^{L/2}: log Z equals enumeration (L=4), every proposal has
     log q = -beta E - log Z, and every proposal is accepted (config: L=8, chi=16, p=0.10)."""
@@ -68,6 +69,7 @@ def test_exact_when_untruncated(tn, precision):
 @pytest.mark.parametrize("precision,L,chi,p", [
     ("fp64", 16, 8, 0.109), ("fp64", 24, 16, 0.109), ("fp64", 13, 5, 0.2),
     ("fp32", 16, 8, 0.109), ("fp32", 24, 16, 0.109),
+    ("tf32", 24, 16, 0.109), ("tf32", 20, 32, 0.109), ("tf32", 40, 32, 0.109),
 ])
 def test_conditionals_and_spins(tn, precision, L, chi, p):
     """Per-site q(+) teacher-forced on the GPU's spins; log q; the spins themselves equal the
