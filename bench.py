@@ -5,10 +5,12 @@ proposals with log q, Metropolis and observables.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Default workload (one GPU): L = 256, chi = 32, p = 0.109 on the Nishimori line,
-64 realizations x 2 chains x 250 proposals (500 proposals per realization), mixed precision
-(FP32 environment build, BF16 cached environments and sampling operands, FP64 log-norms,
-log q and Metropolis).  Under torchrun every rank runs its own 64 realizations (weak
-scaling, no data-path collective).  Prints one JSON line on rank 0.
+64 realizations x 2 chains x 250 proposals (500 proposals per realization) per step, mixed
+precision (FP32 environment build and cache, 3xTF32 tensor-core sampling, FP64 log-norms,
+log q and Metropolis).  Up to --inflight steps run concurrently, one context and CUDA
+stream each (continuous batching: a batch's environment build leaves most SMs free).
+Under torchrun every rank runs its own batches (weak scaling, no data-path collective).
+Prints one JSON line on rank 0.
 """
 import argparse
 import json
@@ -30,7 +32,7 @@ UNIT = "spins/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32", choices=["bf16", "tf32", "fp32", "fp64"])
@@ -40,6 +42,7 @@ def parse():
     ap.add_argument("--n", type=int, default=250, help="proposals per chain per step")
     ap.add_argument("--chains", type=int, default=2)
     ap.add_argument("--p", type=float, default=0.109)
+    ap.add_argument("--inflight", type=int, default=4, help="batches in flight (contexts on streams)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
@@ -194,6 +197,7 @@ def main():
         run_reference(a, rank, world)
         return _finish(world)
 
+    import threading
     import numpy as np
     import torch
     import __graft_entry__
@@ -202,97 +206,124 @@ def main():
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.Stream(device=dev)
-    torch.cuda.set_stream(stream)
     beta = tn.nishimori_beta(a.p)
     R, L = a.R, a.L
+    S = max(1, min(a.inflight, a.steps))          # batches in flight (one context + stream each)
 
     def seeds_for(step):
         base = 1_000_003 * (step + 1) + rank * R
         return np.arange(base, base + R, dtype=np.uint64)
 
-    J0 = tn.couplings_pmj(L, seeds_for(0), a.p, stream=stream)
-    ctx = tn.TNMC(L, J0, [beta] * R, seeds_for(0), a.chi, precision=a.precision, n_chains=a.chains,
-                  n_therm=0, stream=stream)
-
+    streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
+    J0 = tn.couplings_pmj(L, seeds_for(0), a.p)
+    ctxs = [tn.TNMC(L, J0, [beta] * R, seeds_for(0), a.chi, precision=a.precision, n_chains=a.chains,
+                    n_therm=0, stream=streams[i]) for i in range(S)]
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def one_step(step, marks=None):
-        s = seeds_for(step)
-        J = tn.couplings_pmj(L, s, a.p, stream=stream)
-        ctx.set_couplings(J, [beta] * R, s)
-        if marks: marks[0].record(stream)
+    def enqueue(step, i, marks=None):
+        """One step on context i: new realizations (couplings generated on the device),
+        environments, proposals, Metropolis -- all queued on stream i, no host sync."""
+        ctx, st = ctxs[i], streams[i]
+        if marks: marks[0].record(st)
+        ctx.set_realizations(seeds_for(step), [beta] * R, a.p)
         ctx.build_env(return_logz=False)
-        if marks: marks[1].record(stream)
+        if marks: marks[1].record(st)
         ctx.propose(a.n, 0, outputs=False)
-        if marks: marks[2].record(stream)
+        if marks: marks[2].record(st)
         ctx.accept()
-        if marks: marks[3].record(stream)
+        if marks: marks[3].record(st)
 
     for w in range(a.warmup):
-        one_step(w)
+        enqueue(w, w % S)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = Clocks(local)
     clocks.start()
-    launches0 = ctx.launch_count()
+    launches0 = sum(c.launch_count() for c in ctxs)
+    main_st = torch.cuda.current_stream()
     t_start, t_end = ev(), ev()
-    step_ms, phases = [], []
     torch.cuda.synchronize()
-    t_start.record(stream)
+    t_start.record(main_st)
+    for st in streams:
+        st.wait_event(t_start)
+    marks = []
     for k in range(a.steps):
         m = [ev() for _ in range(4)]
-        s0 = ev(); s0.record(stream)
-        one_step(a.warmup + k, m)
-        s1 = ev(); s1.record(stream)
-        step_ms.append((s0, s1))
-        phases.append(m)
-    t_end.record(stream)
+        enqueue(a.warmup + k, k % S, m)
+        marks.append(m)
+    for st in streams:
+        e = ev(); e.record(st); main_st.wait_event(e)
+    t_end.record(main_st)
     torch.cuda.synchronize()
-    # library launches in the timed region, plus the coupling generator kernel of each step
-    gpu_launches = ctx.launch_count() - launches0 + a.steps
+    gpu_launches = sum(c.launch_count() for c in ctxs) - launches0
     elapsed = t_start.elapsed_time(t_end) / 1e3
     if world > 1:
         t = torch.tensor([elapsed], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         elapsed = float(t.item())
     clk = clocks.stop()
-    per_step = [s0.elapsed_time(s1) for s0, s1 in step_ms]
-    build_ms = statistics.mean(m[0].elapsed_time(m[1]) for m in phases)
-    samp_ms = statistics.mean(m[1].elapsed_time(m[2]) for m in phases)
-    acc_ms = statistics.mean(m[2].elapsed_time(m[3]) for m in phases)
-    obs = ctx.observables()
+    per_step = [m[0].elapsed_time(m[3]) for m in marks]
+    build_ms = statistics.mean(m[0].elapsed_time(m[1]) for m in marks)
+    samp_ms = statistics.mean(m[1].elapsed_time(m[2]) for m in marks)
+    acc_ms = statistics.mean(m[2].elapsed_time(m[3]) for m in marks)
+    # union of the device intervals in which an environment build / a sampling sweep ran
+    def union(pairs):
+        iv = sorted((t_start.elapsed_time(x), t_start.elapsed_time(y)) for x, y in pairs)
+        tot, cur = 0.0, None
+        for s0, s1 in iv:
+            if cur is None or s0 > cur[1]:
+                if cur: tot += cur[1] - cur[0]
+                cur = [s0, s1]
+            else:
+                cur[1] = max(cur[1], s1)
+        if cur: tot += cur[1] - cur[0]
+        return tot
+    build_union_ms = union([(m[0], m[1]) for m in marks])
+    samp_union_ms = union([(m[1], m[2]) for m in marks])
+    stats = [c.build_stats() for c in ctxs]
+    mean_sweeps = sum(s_["total_sweeps"] for s_ in stats) / max(1, sum(s_["svds"] for s_ in stats))
+    obs = []
+    for c in ctxs:
+        obs += c.observables()
     dav = tn.disorder_average(obs)
     spins_per_step = R * a.chains * a.n * L * L
     value = world * spins_per_step * a.steps / elapsed
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: one host thread per context,
+    # each step copies its couplings from pinned host memory and reads its observables back
     e2e = None
     if not a.no_e2e:
-        Jh_host = torch.empty((R, 2 * L * (L - 1)), dtype=torch.int8).pin_memory()
-        Jh_host.copy_(J0.cpu())
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        Jhost = [torch.empty((R, 2 * L * (L - 1)), dtype=torch.int8).pin_memory() for _ in range(S)]
+        for jh in Jhost:
+            jh.copy_(J0.cpu())
         k_e2e = max(1, a.steps)
-        for k in range(k_e2e):
-            ctx.set_couplings(Jh_host, [beta] * R, seeds_for(0))
-            ctx.build_env(return_logz=False)
-            ctx.propose(a.n, 0, outputs=False)
-            ctx.accept()
-            _ = ctx.observables()
-        t1 = time.perf_counter()
-        e_el = t1 - t0
+        torch.cuda.synchronize()
+
+        def worker(i):
+            torch.cuda.set_device(local)
+            for k in range(i, k_e2e, S):
+                ctxs[i].set_couplings(Jhost[i], [beta] * R, seeds_for(k))
+                ctxs[i].build_env(return_logz=False)
+                ctxs[i].propose(a.n, 0, outputs=False)
+                ctxs[i].accept()
+                ctxs[i].observables()        # device-to-host read of the step's result
+        t0 = time.perf_counter()
+        ths = [threading.Thread(target=worker, args=(i,)) for i in range(S)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        e_el = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([e_el], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e_el = float(t.item())
         e2e = dict(value=world * spins_per_step * k_e2e / e_el, unit=UNIT,
                    h2d_bytes_per_step=int(R * 2 * L * (L - 1) + 16 * R),
-                   d2h_bytes_per_step=int(R * 112 + 8))
+                   d2h_bytes_per_step=int(R * 112))
 
-    # ---- roofline of the dominant kernel
-    roof = roofline(a, build_ms, samp_ms, tn)
+    roof = roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps)
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
@@ -301,62 +332,71 @@ def main():
         cpu = dict(value=rate, unit=UNIT, cores=cores, kind="oracle", sample=sample)
 
     if rank == 0:
+        cfg = _config(a)
+        cfg["inflight_batches"] = S
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=a.steps, warmup=a.warmup,
                     ms_per_step=1e3 * elapsed / a.steps, higher_is_better=True, scaling="weak",
                     vs_baseline=None, dtype=a.precision,
                     data="synthetic: Philox +-J disorder on the Nishimori line (seeded, no dataset)",
-                    config=_config(a), e2e=e2e, gpu_launches=int(gpu_launches),
+                    config=cfg, e2e=e2e, gpu_launches=int(gpu_launches),
                     roofline=roof, cpu_baseline=cpu, clocks=clk,
                     latency_ms=dict(p50=float(np.percentile(per_step, 50)), p99=float(np.percentile(per_step, 99)),
-                                    unit="per batch of realizations (one step)"),
-                    phases_ms=dict(env_build=build_ms, propose=samp_ms, accept=acc_ms),
+                                    unit="per batch of realizations, queue to Metropolis done"),
+                    phases_ms=dict(env_build=build_ms, propose=samp_ms, accept=acc_ms,
+                                   env_build_busy=build_union_ms, propose_busy=samp_union_ms),
+                    jacobi_mean_sweeps=mean_sweeps,
                     accepted_proposals_per_s=value / (L * L) * dav["acceptance"],
                     acceptance=dav["acceptance"], clamps=dav["clamps"],
                     observables={k: dav[k] for k in ("E", "m2", "q2", "U_m", "Q_q")})
         print(json.dumps(line), flush=True)
-    ctx.close()
+    for c in ctxs:
+        c.close()
     return _finish(world)
 
 
-def roofline(a, build_ms, samp_ms, tn):
+def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
+    """Roofline of the dominant kernel from live CUDA-event timings.  Algorithmic work per
+    launch of the environment build: per site step the MPO product X (8 D^2 CHI flops),
+    the Householder R factor of the 2D x D matrix (10/3 D^3), Q (4 CHI^3), Y = R M (2 D^3),
+    P = M V (2 D^2 CHI) and the one-sided Jacobi SVD at the measured mean sweep count
+    (per sweep D(D-1)/2 pairs x (3 dot products + rotation of two Y and two V columns =
+    12 D + 6 D flops)).  Sampling sweep: bytes of the environment tiles read twice per row
+    per 128-proposal tile plus the per-site workspace written and read back."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    src = "measured" if "hbm_gbs" in peaks else "fallback"
     L, chi = a.L, a.chi
     CHI = 4 if chi <= 4 else 8 if chi <= 8 else 16 if chi <= 16 else 32
-    te = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16": 2}[a.precision]
-    tw = 8 if a.precision == "fp64" else 4
-    items = a.chains * a.n
-    NW = 8
-    tiles = math.ceil(items / NW) * a.R
-    env_bytes = tiles * 2 * L * L * (2 * CHI * CHI) * te          # two sweeps per proposal tile
-    ws_bytes = a.R * items * L * L * (2 * CHI) * tw * 2            # workspace write + read
-    samp_bytes = env_bytes + ws_bytes
-    samp_gbs = samp_bytes / (samp_ms / 1e3) / 1e9
-    # FP32 ALU peak of the build: 152 SMs x 128 lanes x 2 flop x max clock
-    sm_clock = peaks.get("sm_max_mhz", 2070.0) * 1e6
-    alu_peak = 152 * 128 * 2 * sm_clock / 1e12
-    if a.precision == "fp64":
-        alu_peak = alu_peak / 64.0
     D = 2 * CHI
     site_flops = (8 * D * D * CHI + (10.0 / 3.0) * D ** 3 + 4 * CHI ** 3 + 2 * D ** 3 + 2 * D * D * CHI
-                  + 6 * (D * (D - 1) / 2) * (12 * D))            # 6 Jacobi sweeps, nominal
-    build_flops = a.R * (L - 1) * L * site_flops
-    build_tf = build_flops / (build_ms / 1e3) / 1e12
-    dominant = "env_build" if build_ms >= samp_ms else "sample"
-    if dominant == "sample":
-        return dict(kernel="sample_kernel", bound="hbm", achieved=samp_gbs, peak=hbm, unit="GB/s",
-                    frac=samp_gbs / hbm, traffic=None, peak_source=src,
-                    algorithmic_bytes_per_launch=samp_bytes)
+                  + mean_sweeps * (D * (D - 1) / 2) * (18 * D))
+    build_flops = a.R * (L - 1) * L * site_flops                  # per launch (one batch)
+    K = len(marks)
+    sm_clock = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    alu_peak = 152 * 128 * 2 * sm_clock / 1e12                    # FP32 lanes x FMA x clock
+    if a.precision == "fp64":
+        alu_peak = alu_peak / 64.0
+    per_launch_ms = statistics.mean(m[0].elapsed_time(m[1]) for m in marks)
+    build_tf = K * build_flops / (build_union_ms / 1e3) / 1e12
+    te = {"fp64": 8, "fp32": 4, "tf32": 4, "bf16": 2}[a.precision]
+    items = a.chains * a.n
+    M = 128 if a.precision == "tf32" and CHI in (16, 32) else 8
+    tiles = math.ceil(items / M) * a.R
+    samp_bytes = tiles * 2 * L * L * (2 * CHI * CHI) * te + a.R * items * L * L * (2 * CHI) * 4 * 2
+    samp_gbs = K * samp_bytes / (samp_union_ms / 1e3) / 1e9
     return dict(kernel="env_build_kernel", bound="alu", achieved=build_tf, peak=alu_peak, unit="TFLOP/s",
                 frac=build_tf / alu_peak, traffic=None,
-                peak_source="derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock" + (" / 64 (FP64)" if a.precision == "fp64" else ""),
-                algorithmic_flops_per_launch=build_flops,
-                other={"sample_kernel_GBps": samp_gbs, "sample_frac_hbm": samp_gbs / hbm})
+                peak_source=("derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
+                             + (" / 64 (FP64 rate of this part)" if a.precision == "fp64" else "")),
+                algorithmic_flops_per_launch=build_flops, launches=K,
+                per_launch_ms=per_launch_ms, busy_ms=build_union_ms,
+                sampler=dict(kernel="sample_tc_kernel" if M == 128 else "sample_kernel", bound="hbm",
+                             achieved=samp_gbs, peak=hbm, unit="GB/s", frac=samp_gbs / hbm,
+                             algorithmic_bytes_per_launch=samp_bytes, busy_ms=samp_union_ms,
+                             peak_source="measured" if "hbm_gbs" in peaks else "fallback"))
 
 
 def _finish(world):

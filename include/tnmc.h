@@ -108,12 +108,23 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
                         const uint64_t* seeds_host, int chi, const tnmc_opts* opts,
                         tnmc_ctx** out);
 
-/* Replace the disorder realizations of an existing context (same L, n_real, chi): copies
- * new couplings (host or device), inverse temperatures and seeds, resets the chains and
- * marks the environments stale.  Lets one context serve successive batches without
- * re-allocating its caches.  Errors as tnmc_create. */
+/* Replace the disorder realizations of an existing context (same L, n_real, chi): queues
+ * the copy of new couplings (host or device, validated when on the host), inverse
+ * temperatures and seeds on the context's stream, resets the chains and marks the
+ * environments stale, so that one context serves successive batches without re-allocating
+ * its caches.  Asynchronous: beta_host and seeds_host may be reused on return (they go
+ * through a pinned staging ring); a host couplings buffer in pinned memory must stay
+ * unchanged until the stream has executed the copy.  Errors as tnmc_create. */
 tnmc_status tnmc_set_couplings(tnmc_ctx* ctx, const int8_t* couplings, const double* beta_host,
                                const uint64_t* seeds_host);
+
+/* New realizations from seeds alone (Sec. III.A disorder, as tnmc_couplings_pmj): queues the
+ * seeds and inverse temperatures, generates the +-J couplings with probability p of an
+ * antiferromagnetic bond on the device, resets the chains and marks the environments
+ * stale -- all asynchronous on the context's stream (no host synchronisation), so batches
+ * of several contexts on several streams overlap.  Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
+tnmc_status tnmc_set_realizations(tnmc_ctx* ctx, const uint64_t* seeds_host, const double* beta_host,
+                                  double p);
 
 /* (a) Boundary-MPS contraction (Sec. II.B): for r = L-2 .. 0 apply the row-transfer MPO
  * (the T tensors: copy tensor with the Boltzmann matrices W absorbed) to the cached MPS of

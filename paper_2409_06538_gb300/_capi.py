@@ -23,6 +23,7 @@ SIGNATURES = {
     "tnmc_create": (c_int, [c_int, c_int, c_void_p, c_double_p, c_uint64_p, c_int, c_void_p,
                             ctypes.POINTER(c_void_p)]),
     "tnmc_set_couplings": (c_int, [c_void_p, c_void_p, c_double_p, c_uint64_p]),
+    "tnmc_set_realizations": (c_int, [c_void_p, c_uint64_p, c_double_p, c_double]),
     "tnmc_build_env": (c_int, [c_void_p, c_double_p]),
     "tnmc_propose": (c_int, [c_void_p, c_int, ctypes.c_uint64, c_void_p, c_void_p, c_void_p]),
     "tnmc_get_spins": (c_int, [c_void_p, c_void_p]),

@@ -56,6 +56,14 @@ struct tnmc_ctx {
   double* acc = nullptr;
   int* cur_idx = nullptr;
   std::vector<void*> allocs;
+  // pinned staging ring for the small per-batch host inputs (inverse temperatures, seeds),
+  // so that host-to-device copies are truly asynchronous and the caller's buffers can be
+  // reused at once; a slot is reused only after its copy has executed
+  static constexpr int kStageSlots = 8;
+  unsigned char* h_stage = nullptr;
+  cudaEvent_t stage_ev[kStageSlots] = {};
+  bool stage_used[kStageSlots] = {};
+  int stage_next = 0;
 };
 
 static std::string g_create_err;
@@ -232,24 +240,59 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
   return TNMC_OK;
 }
 
+// Queue the copy of n_real inverse temperatures and seeds through the pinned staging ring.
+static tnmc_status stage_small_inputs(tnmc_ctx* c, const double* beta_host, const uint64_t* seeds_host) {
+  for (int k = 0; k < c->n_real; ++k)
+    if (!(beta_host[k] > 0.0) || !std::isfinite(beta_host[k])) return fail(c, TNMC_ERR_ARG, "beta must be positive and finite");
+  const size_t bytes = (size_t)16 * c->n_real;
+  cudaError_t e = cudaSuccess;
+  if (!c->h_stage) {
+    e = cudaMallocHost(reinterpret_cast<void**>(&c->h_stage), bytes * tnmc_ctx::kStageSlots);
+    if (e != cudaSuccess) { cudaGetLastError(); c->h_stage = nullptr; return fail(c, TNMC_ERR_OOM, "pinned staging"); }
+    for (int s = 0; s < tnmc_ctx::kStageSlots; ++s) cudaEventCreateWithFlags(&c->stage_ev[s], cudaEventDisableTiming);
+  }
+  const int slot = c->stage_next;
+  c->stage_next = (slot + 1) % tnmc_ctx::kStageSlots;
+  if (c->stage_used[slot]) {
+    e = cudaEventSynchronize(c->stage_ev[slot]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "staging wait");
+  }
+  unsigned char* h = c->h_stage + bytes * slot;
+  std::memcpy(h, beta_host, sizeof(double) * c->n_real);
+  std::memcpy(h + sizeof(double) * c->n_real, seeds_host, sizeof(uint64_t) * c->n_real);
+  e = cudaMemcpyAsync(c->beta, h, sizeof(double) * c->n_real, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->seeds, h + sizeof(double) * c->n_real, sizeof(uint64_t) * c->n_real, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(c->stage_ev[slot], c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "staging copy");
+  c->stage_used[slot] = true;
+  return TNMC_OK;
+}
+
 tnmc_status tnmc_set_couplings(tnmc_ctx* c, const int8_t* couplings, const double* beta_host,
                                const uint64_t* seeds_host) {
   if (!c || !couplings || !beta_host || !seeds_host) return fail(c, TNMC_ERR_ARG, "NULL argument");
-  for (int k = 0; k < c->n_real; ++k)
-    if (!(beta_host[k] > 0.0) || !std::isfinite(beta_host[k])) return fail(c, TNMC_ERR_ARG, "beta must be positive and finite");
   const size_t nb = (size_t)2 * c->L * (c->L - 1) * c->n_real;
-  cudaError_t e;
-  if (is_device_ptr(couplings)) {
-    e = cudaMemcpyAsync(c->J, couplings, nb, cudaMemcpyDeviceToDevice, c->stream);
-  } else {
+  const bool dev = is_device_ptr(couplings);
+  if (!dev)
     for (size_t i = 0; i < nb; ++i)
       if (couplings[i] != 1 && couplings[i] != -1) return fail(c, TNMC_ERR_ARG, "couplings must be +1 or -1");
-    e = cudaMemcpyAsync(c->J, couplings, nb, cudaMemcpyHostToDevice, c->stream);
-  }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->beta, beta_host, sizeof(double) * c->n_real, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->seeds, seeds_host, sizeof(uint64_t) * c->n_real, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  tnmc_status s = stage_small_inputs(c, beta_host, seeds_host);
+  if (s) return s;
+  cudaError_t e = cudaMemcpyAsync(c->J, couplings, nb, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set couplings");
+  c->env_built = false;
+  return tnmc_reset_chains(c);
+}
+
+tnmc_status tnmc_set_realizations(tnmc_ctx* c, const uint64_t* seeds_host, const double* beta_host, double p) {
+  if (!c || !seeds_host || !beta_host) return fail(c, TNMC_ERR_ARG, "NULL argument");
+  if (!(p >= 0.0 && p <= 1.0)) return fail(c, TNMC_ERR_ARG, "p must be in [0, 1]");
+  tnmc_status s = stage_small_inputs(c, beta_host, seeds_host);
+  if (s) return s;
+  cudaError_t e = tnmc::launch_couplings(c->L, c->n_real, c->seeds, p, c->J, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "couplings launch");
+  ++c->launches;
   c->env_built = false;
   return tnmc_reset_chains(c);
 }
@@ -438,6 +481,10 @@ tnmc_status tnmc_destroy(tnmc_ctx* c) {
   if (!c) return TNMC_OK;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
   for (void* p : c->allocs) cudaFree(p);
+  if (c->h_stage) {
+    cudaFreeHost(c->h_stage);
+    for (int s = 0; s < tnmc_ctx::kStageSlots; ++s) if (c->stage_ev[s]) cudaEventDestroy(c->stage_ev[s]);
+  }
   c->allocs.clear();
   delete c;
   return TNMC_OK;

@@ -116,7 +116,9 @@ __device__ __forceinline__ void prefetch_async(void* smem, const void* gmem, int
 
 template <int CHI> struct EnvCfg {
   static constexpr int D = 2 * CHI;                 // MPO bond x MPS bond
-  static constexpr int NWARP = CHI < 4 ? 4 : (CHI > 16 ? 16 : CHI);   // >= 8*CHI/32 Jacobi lanes
+  // 8 lanes per Jacobi pair (8*CHI threads); CHI = 32 runs 256 threads so that two
+  // realizations fit on one SM (registers and shared memory)
+  static constexpr int NWARP = CHI < 4 ? 4 : (CHI > 8 ? 8 : CHI);
   static constexpr int NT = 32 * NWARP;
   static constexpr int TILE = 2 * CHI * CHI;        // [y][alpha][beta]
 };
@@ -180,7 +182,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
   __shared__ T red[32];
   __shared__ T sig[D];
   __shared__ int sel[CHI];
-  __shared__ int rot[2];
+  __shared__ int rot[3];            // per-sweep 'any rotation' flags, a ring of three
   __shared__ int knext_s;
 
   const int8_t* J = args.J + (size_t)real * 2 * L * (L - 1);
@@ -492,7 +494,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       for (int e = tid; e < DP * n; e += NT) { const int i = e % DP, j = e / DP; Vc[e] = (i == j) ? T(1) : T(0); }
       fro = warp_sum(fro);
       if (lane == 0) red[warp] = fro;
-      if (tid == 0) { rot[0] = 0; rot[1] = 0; }
+      if (tid == 0) { rot[0] = 0; rot[1] = 0; rot[2] = 0; }
       __syncthreads();
       if (warp == 0) {
         T f = lane < NWARP ? red[lane] : T(0);
@@ -517,7 +519,10 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
         const bool active = w < n / 2;
         const int m1 = n - 1;
         for (; sweep < JacobiTol<T>::maxsw; ++sweep) {
-          if (tid == 0) rot[(sweep + 1) & 1] = 0;
+          // clear the flag of sweep+1; the slot was last read at the end of sweep-2, and every
+          // thread has passed a barrier of sweep-1 since (a two-slot ring would let a slow
+          // thread read a flag that was already cleared and leave the loop alone)
+          if (tid == 0) rot[(sweep + 1) % 3] = 0;
           // round-robin pair of slot w in round 0; each later round adds 1 (mod n-1) to
           // both members, except that slot 0 keeps column n-1
           int p = 0, q = 0;
@@ -560,11 +565,11 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
                 vp[li + 8 * k] = wp[k];
                 vq[li + 8 * k] = wq[k];
               }
-              if (li == 0) rot[sweep & 1] = 1;
+              if (li == 0) rot[sweep % 3] = 1;
             }
             named_barrier(1, NJ);
           }
-          if (rot[sweep & 1] == 0) break;
+          if (rot[sweep % 3] == 0) break;
         }
       }
       __syncthreads();

@@ -78,6 +78,13 @@ class TNMC:
                                               seeds.ctypes.data_as(_capi.c_uint64_p)))
         self._keep = (J, beta, seeds)
 
+    def set_realizations(self, seeds, beta, p):
+        """New realizations from seeds: couplings generated on the device, asynchronously."""
+        seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+        beta = np.ascontiguousarray(np.broadcast_to(np.asarray(beta, dtype=np.float64), (self.n_real,)))
+        self._chk(self.lib.tnmc_set_realizations(self.ctx, seeds.ctypes.data_as(_capi.c_uint64_p),
+                                                 beta.ctypes.data_as(_capi.c_double_p), float(p)))
+
     def _chk(self, code):
         _capi.check(code, self.ctx)
 

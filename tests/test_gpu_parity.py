@@ -221,6 +221,28 @@ def test_observables_match_independent_oracle_run(tn):
     assert abs(g["U_m"] - o["U_m"]) < 0.05
 
 
+def test_set_realizations_reuses_a_context(tn):
+    """New seeds on an existing context (couplings generated on the device, asynchronously)
+    give the same environments as a fresh context and as the oracle, twice in a row."""
+    L, p, chi = 12, 0.109, 8
+    beta = lattice.nishimori_beta(p)
+    ctx = _ctx(tn, L, p, chi, [1, 2, 3], "fp64")
+    ctx.build_env()
+    for seeds in ([10, 11, 12], [7, 8, 9]):
+        ctx.set_realizations(seeds, [beta] * 3, p)
+        lz = ctx.build_env()
+        fresh = _ctx(tn, L, p, chi, seeds, "fp64")
+        lz_fresh = fresh.build_env()
+        fresh.close()
+        assert np.abs(lz - lz_fresh).max() == 0.0
+        for k, s in enumerate(seeds):
+            assert abs(lz[k] - oracle_envs(s, L, p, chi).log_z) < 1e-11 * abs(lz[k])
+        out = ctx.propose(3, 0)
+        ctx.accept()
+        assert np.isfinite(out["logq"].cpu().numpy()).all()
+    ctx.close()
+
+
 def test_argument_errors(tn):
     from paper_2409_06538_gb300 import _capi
     L = 4
