@@ -286,7 +286,11 @@ def main():
     obs = []
     for c in ctxs:
         obs += c.observables()
-    dav = tn.disorder_average(obs)
+    if world > 1:       # the one cross-rank exchange: per-realization means for [.] averages
+        from paper_2409_06538_gb300 import shard
+        dav, _ = shard.gather_disorder_average(obs)
+    else:
+        dav = tn.disorder_average(obs)
     spins_per_step = R * a.chains * a.n * L * L
     value = world * spins_per_step * a.steps / elapsed
 
