@@ -46,6 +46,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving measurement: a Poisson request stream through the request server")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
+    ap.add_argument("--serve-Ls", default="16,32,64,128,256,512")
+    ap.add_argument("--serve-chi-max", type=int, default=32)
+    ap.add_argument("--serve-inflight", type=int, default=32)
+    ap.add_argument("--serve-linger-ms", type=float, default=20.0)
     return ap.parse_args()
 
 
@@ -195,6 +203,12 @@ def main():
         dist.init_process_group(backend)
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return _finish(world)
+    if a.serve:
+        if rank == 0:
+            rc = run_serve(a)
+            if world == 1:
+                return rc
         return _finish(world)
 
     import threading
@@ -401,6 +415,86 @@ def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
                              achieved=samp_gbs, peak=hbm, unit="GB/s", frac=samp_gbs / hbm,
                              algorithmic_bytes_per_launch=samp_bytes, busy_ms=samp_union_ms,
                              peak_source="measured" if "hbm_gbs" in peaks else "fallback"))
+
+
+def run_serve(a):
+    """Poisson stream of independent requests (seed, L, p, beta, chi, n_samples): L uniform over
+    --serve-Ls, p uniform in [0.09, 0.13] with beta on the Nishimori line, chi = min(chi_max,
+    2^(L/2)), n_samples uniform in [100, 1000].  Prints one JSON line: proposed spins per second
+    over the makespan (first arrival to last completion) and per-request latency percentiles."""
+    # one hardware queue per in-flight batch: with fewer queues than streams, a short batch
+    # can wait behind a long one that shares its queue
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2409_06538_gb300 as tn
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(20240911)
+    Ls = [int(x) for x in a.serve_Ls.split(",")]
+    N = a.serve_requests
+    gaps = rng.exponential(1.0 / a.serve_rate, N)
+    reqs = []
+    for k in range(N):
+        L = int(rng.choice(Ls))
+        p = float(rng.uniform(0.09, 0.13))
+        chi = int(min(a.serve_chi_max, 2 ** (L // 2)))
+        reqs.append((10_000 + k, L, chi, p, tn.nishimori_beta(p), int(rng.integers(100, 1001))))
+    clocks = Clocks(0)
+    srv = tn.TNMCServer(a.precision, a.chains, 0, chunk=256, max_batch=64, max_inflight=a.serve_inflight,
+                        linger_us=int(a.serve_linger_ms * 1000))
+    clocks.start()
+    t0 = srv.now()
+    ids = []
+    for k, r in enumerate(reqs):
+        target = t0 + gaps[: k + 1].sum()
+        while srv.now() < target:
+            time.sleep(min(0.001, max(0.0, target - srv.now())))
+        ids.append(srv.submit(*r))
+    srv.drain()
+    res = {}
+    while len(res) < N:
+        for r in srv.poll(512):
+            res[r["id"]] = r
+    st = srv.stats()
+    last_err = srv.last_error()
+    srv.close()
+    ck = clocks.stop()
+    bad = [r for r in res.values() if r["status"] != 0]
+    L_of = {i: reqs[k][1] for k, i in enumerate(ids)}
+    fails = {}
+    for r in bad:
+        key = f"L={L_of[r['id']]} status={r['status']}"
+        fails[key] = fails.get(key, 0) + 1
+    lat = np.array([res[i]["latency"] for i in ids])
+    t_first = min(r["t_submit"] for r in res.values())
+    t_last = max(r["t_done"] for r in res.values())
+    span = t_last - t_first
+    spins = sum(res[i]["n_prop"] * reqs[k][1] ** 2 for k, i in enumerate(ids))
+    acc = sum(res[i]["n_acc"] for i in ids)
+    by_L = {}
+    for k, i in enumerate(ids):
+        by_L.setdefault(reqs[k][1], []).append(res[i]["latency"])
+    line = {
+        "metric": "spins proposed/s under a Poisson request stream (continuous batching)",
+        "value": spins / span, "unit": UNIT, "mode": "serve", "n_gpus": 1, "higher_is_better": True,
+        "dtype": {"tf32": "f32+tf32", "fp32": "f32", "fp64": "f64", "bf16": "f32+bf16"}[a.precision],
+        "data": "synthetic",
+        "config": {"workload": f"Poisson {a.serve_rate:g} req/s, {N} requests, L in {Ls}, "
+                               f"chi=min({a.serve_chi_max},2^(L/2)), p in [0.09,0.13] Nishimori, "
+                               f"n_samples in [100,1000], {a.chains} chains, {a.precision}",
+                   "max_inflight": a.serve_inflight, "linger_ms": a.serve_linger_ms, "chunk": 256,
+                   "max_batch": 64},
+        "makespan_s": span, "accepted_per_s": acc / span, "failed": len(bad), "failures": fails,
+        "last_error": last_err,
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "latency_p50_by_L": {str(L): float(np.median(v)) for L, v in sorted(by_L.items())},
+        "server": st, "gpu_launches": st["launches"], "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if not bad else 1
 
 
 def _finish(world):

@@ -224,6 +224,97 @@ tnmc_status tnmc_build_env_noalloc(int L, int n_real, int chi, int precision,
 /* Kernel launch accounting: number of kernels this context launched since creation. */
 int64_t tnmc_launch_count(const tnmc_ctx* ctx);
 
+/* Device memory accounting.  tnmc_device_bytes: bytes the context holds now (its buffers
+ * grow once to the largest n passed to tnmc_propose).  tnmc_estimate_device_bytes: bytes a
+ * context of these arguments would hold after proposals of up to n_max per chain, without
+ * allocating anything (0 for invalid arguments); it uses the current device's SM count, or
+ * 152 when no device is present. */
+size_t tnmc_device_bytes(const tnmc_ctx* ctx);
+size_t tnmc_estimate_device_bytes(int L, int n_real, int chi, const tnmc_opts* opts, int n_max);
+
+/* ------------------------------------------------------------------------------------------
+ * Request server: continuous batching of independent realizations on one GPU.
+ *
+ * The paper runs its disorder realizations as fixed sets (Sec. III); each realization is an
+ * independent problem: couplings (Sec. III.A), environments (Sec. II.B), proposals with
+ * log q (Sec. II.C), Metropolis and observables (Sec. III.C).  The server takes such
+ * problems one request at a time from any thread, groups requests of equal (L, chi) into
+ * batches of up to max_batch, runs up to max_inflight batches at once (one pooled context and
+ * CUDA stream each) and returns per-request results as they finish.  A native scheduler
+ * thread makes every CUDA call.  Pooled contexts are kept for reuse and evicted, least
+ * recently used first, when a new (L, chi) needs room within mem_budget; a batch's capacity
+ * is halved until one context fits the budget.
+ *
+ * A request's result does not depend on the batch it ran in: draws are keyed by its seed
+ * and counted by (site, step, chain), sampling runs in fixed steps of `chunk` proposals per
+ * chain, and the Metropolis kernel stops each realization at its own n_samples.  The same
+ * request, server options and library give the same bits alone or in any mix.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct tnmc_server tnmc_server;
+
+typedef struct {
+  int precision;     /* tnmc_precision of every request */
+  int n_chains;      /* independent chains per realization, 1..8 */
+  int n_therm;       /* leading proposals per chain left out of the observables */
+  int chunk;         /* proposals per chain per sampling launch (>= 1) */
+  int max_batch;     /* most realizations in one batch (>= 1) */
+  int max_inflight;  /* most batches on the device at once (>= 1) */
+  int linger_us;     /* a batch short of max_batch waits up to this long for more requests */
+  int device;        /* CUDA device ordinal */
+  size_t mem_budget; /* device bytes all pooled contexts may hold; 0 = 90% of free memory */
+} tnmc_server_opts;
+
+typedef struct {
+  uint64_t seed;     /* realization seed: couplings and every draw (as in tnmc_couplings_pmj) */
+  int L;             /* lattice side, 2..4096 */
+  int chi;           /* MPS bond dimension, 1..32 */
+  double p;          /* probability of an antiferromagnetic bond, [0, 1] */
+  double beta;       /* inverse temperature, finite and > 0 */
+  int n_samples;     /* proposals per chain, >= 1 */
+} tnmc_request;
+
+typedef struct {
+  int64_t id;
+  int32_t status;          /* tnmc_status of this request */
+  int32_t batch_size;      /* realizations in the batch it ran in (0: never launched) */
+  double log_z;            /* log Z~ of its environment build */
+  tnmc_obs obs;            /* thermal means, as tnmc_observables */
+  int64_t build_stats[4];  /* as tnmc_build_stats, for this realization */
+  double t_submit, t_start, t_done;  /* seconds on the server clock (tnmc_server_now) */
+} tnmc_result;
+
+/* Start a server (and its scheduler thread) on opts->device.  TNMC_ERR_ARG for invalid
+ * options, TNMC_ERR_CUDA if the device cannot be queried.  Contexts are made lazily. */
+tnmc_status tnmc_server_create(const tnmc_server_opts* opts, tnmc_server** out);
+
+/* Queue one request; *id_out gets its id (> 0).  Thread-safe, never blocks on the GPU.
+ * TNMC_ERR_ARG for a request outside the ranges above, TNMC_ERR_STATE while stopping. */
+tnmc_status tnmc_server_submit(tnmc_server* srv, const tnmc_request* req, int64_t* id_out);
+
+/* Move up to max_results finished results (in completion order) into out_host; returns
+ * how many.  Thread-safe, non-blocking. */
+int tnmc_server_poll(tnmc_server* srv, tnmc_result* out_host, int max_results);
+
+/* Block until request `id` finishes (timeout_s < 0: no limit), then move its result into
+ * out_host.  TNMC_ERR_TIMEOUT if it did not finish in time or was already collected. */
+tnmc_status tnmc_server_wait(tnmc_server* srv, int64_t id, double timeout_s, tnmc_result* out_host);
+
+/* Block until every submitted request has finished (results stay to be collected). */
+tnmc_status tnmc_server_drain(tnmc_server* srv, double timeout_s);
+
+/* out_host[8]: submitted, completed, failed, batches launched, contexts created, contexts
+ * evicted, peak device bytes held by pooled contexts, kernels launched. */
+tnmc_status tnmc_server_stats(tnmc_server* srv, int64_t* out_host);
+
+/* Text of the last error; a copy owned by the calling thread, valid until its next call. */
+const char* tnmc_server_last_error(tnmc_server* srv);
+
+/* Seconds since tnmc_server_create on the server's steady clock. */
+double tnmc_server_now(tnmc_server* srv);
+
+/* Finish every queued request, stop the scheduler and free all pooled contexts. */
+tnmc_status tnmc_server_destroy(tnmc_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,17 @@ SIGNATURES = {
     "tnmc_build_stats": (c_int, [c_void_p, c_int64_p]),
     "tnmc_build_env_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                                        c_void_p, c_void_p, c_void_p]),
+    "tnmc_device_bytes": (c_size_t, [c_void_p]),
+    "tnmc_estimate_device_bytes": (c_size_t, [c_int, c_int, c_int, c_void_p, c_int]),
+    "tnmc_server_create": (c_int, [c_void_p, ctypes.POINTER(c_void_p)]),
+    "tnmc_server_submit": (c_int, [c_void_p, c_void_p, c_int64_p]),
+    "tnmc_server_poll": (c_int, [c_void_p, c_void_p, c_int]),
+    "tnmc_server_wait": (c_int, [c_void_p, c_int64, c_double, c_void_p]),
+    "tnmc_server_drain": (c_int, [c_void_p, c_double]),
+    "tnmc_server_stats": (c_int, [c_void_p, c_int64_p]),
+    "tnmc_server_last_error": (ctypes.c_char_p, [c_void_p]),
+    "tnmc_server_now": (c_double, [c_void_p]),
+    "tnmc_server_destroy": (c_int, [c_void_p]),
 }
 
 
@@ -51,6 +62,23 @@ class Obs(ctypes.Structure):
                 ("clamps", c_int64), ("E", c_double), ("E2", c_double), ("m_abs", c_double),
                 ("m2", c_double), ("m4", c_double), ("q", c_double), ("q_abs", c_double),
                 ("q2", c_double), ("q4", c_double)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("n_chains", c_int), ("n_therm", c_int), ("chunk", c_int),
+                ("max_batch", c_int), ("max_inflight", c_int), ("linger_us", c_int), ("device", c_int),
+                ("mem_budget", c_size_t)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("L", c_int), ("chi", c_int), ("p", c_double), ("beta", c_double),
+                ("n_samples", c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", c_int64), ("status", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("log_z", c_double),
+                ("obs", Obs), ("build_stats", c_int64 * 4), ("t_submit", c_double), ("t_start", c_double),
+                ("t_done", c_double)]
 
 
 class TnmcError(RuntimeError):

@@ -6,14 +6,21 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/tnmc.h"
 #include "kernels.h"
+#include "ctx_internal.h"
 
 struct tnmc_ctx {
   int L = 0, n_real = 0, chi = 0, CHI = 0, precision = 0, n_chains = 1, n_therm = 0;
+  int cap = 0;                    // realizations allocated; n_real <= cap are active
+  double* pvec = nullptr;         // per-realization antiferromagnetic-bond probability
+  int* nlimit = nullptr;          // per-realization number of proposals the chains use
+  bool use_nlimit = false;
   cudaStream_t stream = nullptr;
   int device = 0, num_sms = 0;
   std::string err;
@@ -56,6 +63,10 @@ struct tnmc_ctx {
   double* acc = nullptr;
   int* cur_idx = nullptr;
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_sizes;
+  // device buffers come from the stream-ordered allocator where the device has one, so that
+  // freeing a context never waits for work on other streams (cudaFree synchronises the device)
+  bool async_alloc = false;
   // pinned staging ring for the small per-batch host inputs (inverse temperatures, seeds),
   // so that host-to-device copies are truly asynchronous and the caller's buffers can be
   // reused at once; a slot is reused only after its copy has executed
@@ -83,13 +94,14 @@ template <typename P>
 tnmc_status dalloc(tnmc_ctx* c, P** p, size_t bytes) {
   void* q = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&q, bytes);
+  cudaError_t e = c->async_alloc ? cudaMallocAsync(&q, bytes, c->stream) : cudaMalloc(&q, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(c, TNMC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
                                      cudaGetErrorString(e));
   }
   c->allocs.push_back(q);
+  c->alloc_sizes.push_back(bytes);
   *p = reinterpret_cast<P*>(q);
   return TNMC_OK;
 }
@@ -97,8 +109,12 @@ tnmc_status dalloc(tnmc_ctx* c, P** p, size_t bytes) {
 void dfree(tnmc_ctx* c, void* p) {
   if (!p) return;
   for (size_t i = 0; i < c->allocs.size(); ++i)
-    if (c->allocs[i] == p) { c->allocs.erase(c->allocs.begin() + i); break; }
-  cudaFree(p);
+    if (c->allocs[i] == p) {
+      c->allocs.erase(c->allocs.begin() + i);
+      c->alloc_sizes.erase(c->alloc_sizes.begin() + i);
+      break;
+    }
+  if (c->async_alloc) cudaFreeAsync(p, c->stream); else cudaFree(p);
 }
 
 int round_chi(int chi) {
@@ -127,11 +143,55 @@ tnmc_status check_status(tnmc_ctx* c) {
   return TNMC_OK;
 }
 
+// Device bytes of every buffer a context holds, one function for the allocation and the
+// capacity estimate so that the two cannot drift apart.
+struct CtxSizes {
+  size_t J, beta, seeds, pvec, nlimit, env, kdim, dqr, lam, logz, rowbuf, Rstore, stats, status, work,
+      work_tc, clamps, have_state, cur_logq, cur_energy, cur_magnet, cur_spins, acc;
+  size_t total() const {
+    return J + beta + seeds + pvec + nlimit + env + kdim + dqr + lam + logz + rowbuf + Rstore + stats + status +
+           work + work_tc + clamps + have_state + cur_logq + cur_energy + cur_magnet + cur_spins + acc;
+  }
+};
+
+CtxSizes ctx_sizes(int L, int n_real, int CHI, int precision, int n_chains, int num_sms) {
+  CtxSizes z{};
+  const size_t tsz = precision == TNMC_FP64 ? 8 : 4;
+  const size_t tesz = precision == TNMC_FP64 ? 8 : (precision == TNMC_MIXED_BF16 ? 2 : 4);
+  const size_t D = 2 * (size_t)CHI, tile = (size_t)2 * CHI * CHI, R = (size_t)n_real;
+  const size_t chains = R * n_chains, words = ((size_t)L * L + 31) / 32;
+  z.J = (size_t)2 * L * (L - 1) * R;
+  z.beta = 8 * R; z.seeds = 8 * R; z.pvec = 8 * R; z.nlimit = 4 * R;
+  z.env = R * L * L * tile * tesz;
+  z.kdim = 4 * R * L * (L + 1);
+  z.dqr = 4 * R * (L + 1);
+  z.lam = 8 * R * L;
+  z.logz = 8 * R;
+  z.rowbuf = R * 2 * L * tile * tsz;
+  z.Rstore = R * L * D * D * tsz;
+  z.stats = 4 * sizeof(long long) * R;
+  z.status = sizeof(unsigned);
+  z.work = tnmc::sample_work_bytes(L, CHI, precision, num_sms);
+  z.work_tc = (precision == TNMC_MIXED_TF32 && tnmc::sample_tc_supported(CHI))
+                  ? tnmc::sample_tc_work_bytes(L, CHI, num_sms) : 0;
+  z.clamps = 8 * R;
+  z.have_state = 4 * chains; z.cur_logq = 8 * chains; z.cur_energy = 4 * chains; z.cur_magnet = 4 * chains;
+  z.cur_spins = 4 * chains * words;
+  z.acc = 8 * R * tnmc::ACC_SLOTS;
+  return z;
+}
+
+// Device bytes of the proposal buffers for n proposals per chain.
+size_t props_bytes(int L, int n_real, int n_chains, int n) {
+  const size_t items = (size_t)n_real * n_chains * n, words = ((size_t)L * L + 31) / 32;
+  return items * (words * 4 + 8 + 4 + 4 + 4);
+}
+
 tnmc_status ensure_props(tnmc_ctx* c, int n) {
   if (n <= c->cap_n) return TNMC_OK;
   dfree(c, c->packed); dfree(c, c->logq); dfree(c, c->energy); dfree(c, c->magnet); dfree(c, c->cur_idx);
   c->packed = nullptr; c->logq = nullptr; c->energy = nullptr; c->magnet = nullptr; c->cur_idx = nullptr;
-  const size_t items = (size_t)c->n_real * c->n_chains * n;
+  const size_t items = (size_t)c->cap * c->n_chains * n;
   tnmc_status s;
   if ((s = dalloc(c, &c->packed, items * c->words * sizeof(uint32_t)))) return s;
   if ((s = dalloc(c, &c->logq, items * sizeof(double)))) return s;
@@ -143,6 +203,7 @@ tnmc_status ensure_props(tnmc_ctx* c, int n) {
 }
 
 }  // namespace
+
 
 extern "C" {
 
@@ -190,42 +251,46 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
     if (Jh[i] != 1 && Jh[i] != -1) return fail(nullptr, TNMC_ERR_ARG, "couplings must be +1 or -1");
 
   tnmc_ctx* c = new tnmc_ctx();
-  c->L = L; c->n_real = n_real; c->chi = chi; c->CHI = round_chi(chi);
+  c->L = L; c->n_real = n_real; c->cap = n_real; c->chi = chi; c->CHI = round_chi(chi);
   c->precision = opts->precision; c->n_chains = opts->n_chains; c->n_therm = opts->n_therm;
   c->stream = reinterpret_cast<cudaStream_t>(opts->stream);
   c->words = (L * L + 31) / 32;
   cudaGetDevice(&c->device);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  int pools = 0;
+  if (cudaDeviceGetAttribute(&pools, cudaDevAttrMemoryPoolsSupported, c->device) != cudaSuccess) cudaGetLastError();
+  c->async_alloc = pools != 0;
   c->t_size = c->precision == TNMC_FP64 ? 8 : 4;
   c->te_size = c->precision == TNMC_FP64 ? 8 : (c->precision == TNMC_MIXED_BF16 ? 2 : 4);
-  const int CHI = c->CHI, D = 2 * CHI;
-  const size_t tile = (size_t)2 * CHI * CHI;
+  const int CHI = c->CHI;
+  const CtxSizes z = ctx_sizes(L, n_real, CHI, c->precision, c->n_chains, c->num_sms);
   tnmc_status s;
 #define TRY(x) do { if ((s = (x)) != TNMC_OK) { g_create_err = c->err; tnmc_destroy(c); return s; } } while (0)
-  TRY(dalloc(c, &c->J, nb * n_real));
-  TRY(dalloc(c, &c->beta, sizeof(double) * n_real));
-  TRY(dalloc(c, &c->seeds, sizeof(uint64_t) * n_real));
-  c->env_bytes = (size_t)n_real * L * L * tile * c->te_size;
-  TRY(dalloc(c, &c->env, c->env_bytes));
-  TRY(dalloc(c, &c->kdim, sizeof(int) * (size_t)n_real * L * (L + 1)));
-  TRY(dalloc(c, &c->dqr, sizeof(int) * (size_t)n_real * (L + 1)));
-  TRY(dalloc(c, &c->lam, sizeof(double) * (size_t)n_real * L));
-  TRY(dalloc(c, &c->logz, sizeof(double) * n_real));
-  TRY(dalloc(c, &c->rowbuf, (size_t)n_real * 2 * L * tile * c->t_size));
-  TRY(dalloc(c, &c->Rstore, (size_t)n_real * L * D * D * c->t_size));
-  TRY(dalloc(c, &c->stats, sizeof(long long) * 4 * n_real));
-  TRY(dalloc(c, &c->status, sizeof(unsigned)));
-  TRY(dalloc(c, &c->work, tnmc::sample_work_bytes(L, CHI, c->precision, c->num_sms)));
-  if (c->precision == TNMC_MIXED_TF32 && tnmc::sample_tc_supported(CHI))
-    TRY(dalloc(c, &c->work_tc, tnmc::sample_tc_work_bytes(L, CHI, c->num_sms)));
-  TRY(dalloc(c, &c->clamps, sizeof(int64_t) * n_real));
+  TRY(dalloc(c, &c->J, z.J));
+  TRY(dalloc(c, &c->beta, z.beta));
+  TRY(dalloc(c, &c->seeds, z.seeds));
+  TRY(dalloc(c, &c->pvec, z.pvec));
+  TRY(dalloc(c, &c->nlimit, z.nlimit));
+  c->env_bytes = z.env;
+  TRY(dalloc(c, &c->env, z.env));
+  TRY(dalloc(c, &c->kdim, z.kdim));
+  TRY(dalloc(c, &c->dqr, z.dqr));
+  TRY(dalloc(c, &c->lam, z.lam));
+  TRY(dalloc(c, &c->logz, z.logz));
+  TRY(dalloc(c, &c->rowbuf, z.rowbuf));
+  TRY(dalloc(c, &c->Rstore, z.Rstore));
+  TRY(dalloc(c, &c->stats, z.stats));
+  TRY(dalloc(c, &c->status, z.status));
+  TRY(dalloc(c, &c->work, z.work));
+  if (z.work_tc) TRY(dalloc(c, &c->work_tc, z.work_tc));
+  TRY(dalloc(c, &c->clamps, z.clamps));
   const size_t chains = (size_t)n_real * c->n_chains;
-  TRY(dalloc(c, &c->have_state, sizeof(int) * chains));
-  TRY(dalloc(c, &c->cur_logq, sizeof(double) * chains));
-  TRY(dalloc(c, &c->cur_energy, sizeof(int32_t) * chains));
-  TRY(dalloc(c, &c->cur_magnet, sizeof(int32_t) * chains));
-  TRY(dalloc(c, &c->cur_spins, sizeof(uint32_t) * chains * c->words));
-  TRY(dalloc(c, &c->acc, sizeof(double) * (size_t)n_real * tnmc::ACC_SLOTS));
+  TRY(dalloc(c, &c->have_state, z.have_state));
+  TRY(dalloc(c, &c->cur_logq, z.cur_logq));
+  TRY(dalloc(c, &c->cur_energy, z.cur_energy));
+  TRY(dalloc(c, &c->cur_magnet, z.cur_magnet));
+  TRY(dalloc(c, &c->cur_spins, z.cur_spins));
+  TRY(dalloc(c, &c->acc, z.acc));
 #undef TRY
   cudaError_t e = cudaMemcpyAsync(c->J, Jh.data(), Jh.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->beta, beta_host, sizeof(double) * n_real, cudaMemcpyHostToDevice, c->stream);
@@ -240,15 +305,18 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
   return TNMC_OK;
 }
 
-// Queue the copy of n_real inverse temperatures and seeds through the pinned staging ring.
-static tnmc_status stage_small_inputs(tnmc_ctx* c, const double* beta_host, const uint64_t* seeds_host) {
-  for (int k = 0; k < c->n_real; ++k)
+// Queue the copy of the small per-realization host inputs (inverse temperatures, seeds and,
+// when given, bond probabilities and proposal limits) through the pinned staging ring.
+static tnmc_status stage_small_inputs(tnmc_ctx* c, const double* beta_host, const uint64_t* seeds_host,
+                                      const double* p_host = nullptr, const int* nlimit_host = nullptr) {
+  const int n = c->n_real;
+  for (int k = 0; k < n; ++k)
     if (!(beta_host[k] > 0.0) || !std::isfinite(beta_host[k])) return fail(c, TNMC_ERR_ARG, "beta must be positive and finite");
-  const size_t bytes = (size_t)16 * c->n_real;
+  const size_t slot_bytes = (size_t)32 * c->cap;
   cudaError_t e = cudaSuccess;
   if (!c->h_stage) {
-    e = cudaMallocHost(reinterpret_cast<void**>(&c->h_stage), bytes * tnmc_ctx::kStageSlots);
-    if (e != cudaSuccess) { cudaGetLastError(); c->h_stage = nullptr; return fail(c, TNMC_ERR_OOM, "pinned staging"); }
+    c->h_stage = static_cast<unsigned char*>(tnmc::pinned_get(slot_bytes * tnmc_ctx::kStageSlots));
+    if (!c->h_stage) return fail(c, TNMC_ERR_OOM, "pinned staging");
     for (int s = 0; s < tnmc_ctx::kStageSlots; ++s) cudaEventCreateWithFlags(&c->stage_ev[s], cudaEventDisableTiming);
   }
   const int slot = c->stage_next;
@@ -257,12 +325,23 @@ static tnmc_status stage_small_inputs(tnmc_ctx* c, const double* beta_host, cons
     e = cudaEventSynchronize(c->stage_ev[slot]);
     if (e != cudaSuccess) return cuda_fail(c, e, "staging wait");
   }
-  unsigned char* h = c->h_stage + bytes * slot;
-  std::memcpy(h, beta_host, sizeof(double) * c->n_real);
-  std::memcpy(h + sizeof(double) * c->n_real, seeds_host, sizeof(uint64_t) * c->n_real);
-  e = cudaMemcpyAsync(c->beta, h, sizeof(double) * c->n_real, cudaMemcpyHostToDevice, c->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->seeds, h + sizeof(double) * c->n_real, sizeof(uint64_t) * c->n_real, cudaMemcpyHostToDevice, c->stream);
+  unsigned char* h = c->h_stage + slot_bytes * slot;
+  unsigned char* hb = h;
+  unsigned char* hs = h + 8 * (size_t)c->cap;
+  unsigned char* hp = h + 16 * (size_t)c->cap;
+  unsigned char* hl = h + 24 * (size_t)c->cap;
+  std::memcpy(hb, beta_host, sizeof(double) * n);
+  std::memcpy(hs, seeds_host, sizeof(uint64_t) * n);
+  e = cudaMemcpyAsync(c->beta, hb, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->seeds, hs, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && p_host) {
+    std::memcpy(hp, p_host, sizeof(double) * n);
+    e = cudaMemcpyAsync(c->pvec, hp, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream);
+  }
+  if (e == cudaSuccess && nlimit_host) {
+    std::memcpy(hl, nlimit_host, sizeof(int) * n);
+    e = cudaMemcpyAsync(c->nlimit, hl, sizeof(int) * n, cudaMemcpyHostToDevice, c->stream);
+  }
   if (e == cudaSuccess) e = cudaEventRecord(c->stage_ev[slot], c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "staging copy");
   c->stage_used[slot] = true;
@@ -282,6 +361,7 @@ tnmc_status tnmc_set_couplings(tnmc_ctx* c, const int8_t* couplings, const doubl
   cudaError_t e = cudaMemcpyAsync(c->J, couplings, nb, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set couplings");
   c->env_built = false;
+  c->use_nlimit = false;
   return tnmc_reset_chains(c);
 }
 
@@ -290,6 +370,7 @@ tnmc_status tnmc_set_realizations(tnmc_ctx* c, const uint64_t* seeds_host, const
   if (!(p >= 0.0 && p <= 1.0)) return fail(c, TNMC_ERR_ARG, "p must be in [0, 1]");
   tnmc_status s = stage_small_inputs(c, beta_host, seeds_host);
   if (s) return s;
+  c->use_nlimit = false;
   cudaError_t e = tnmc::launch_couplings(c->L, c->n_real, c->seeds, p, c->J, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "couplings launch");
   ++c->launches;
@@ -423,6 +504,7 @@ tnmc_status tnmc_accept(tnmc_ctx* c, uint8_t* accepted_dev, int64_t* n_accepted_
   a.accepted = accepted_dev; a.have_state = c->have_state; a.cur_logq = c->cur_logq;
   a.cur_energy = c->cur_energy; a.cur_magnet = c->cur_magnet; a.cur_spins = c->cur_spins;
   a.acc = c->acc; a.cur_idx = c->cur_idx; a.status = c->status;
+  a.nlimit = c->use_nlimit ? c->nlimit : nullptr;
   cudaError_t e = tnmc::launch_accept(a, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "accept launch");
   ++c->launches;
@@ -448,21 +530,7 @@ tnmc_status tnmc_observables(tnmc_ctx* c, tnmc_obs* out_host) {
   cudaError_t e = cudaMemcpy(acc.data(), c->acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(cl.data(), c->clamps, cl.size() * sizeof(int64_t), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "observables copy");
-  for (int k = 0; k < c->n_real; ++k) {
-    const double* a = &acc[(size_t)k * tnmc::ACC_SLOTS];
-    tnmc_obs& o = out_host[k];
-    std::memset(&o, 0, sizeof(o));
-    o.n_prop = (int64_t)llround(a[tnmc::ACC_NPROP]);
-    o.n_acc = (int64_t)llround(a[tnmc::ACC_NACC]);
-    o.n_meas = (int64_t)llround(a[tnmc::ACC_NMEAS]);
-    o.n_meas_q = (int64_t)llround(a[tnmc::ACC_NMEASQ]);
-    o.clamps = cl[k];
-    const double nm = a[tnmc::ACC_NMEAS] > 0 ? a[tnmc::ACC_NMEAS] : 1.0;
-    const double nq = a[tnmc::ACC_NMEASQ] > 0 ? a[tnmc::ACC_NMEASQ] : 1.0;
-    o.E = a[tnmc::ACC_E] / nm; o.E2 = a[tnmc::ACC_E2] / nm; o.m_abs = a[tnmc::ACC_MABS] / nm;
-    o.m2 = a[tnmc::ACC_M2] / nm; o.m4 = a[tnmc::ACC_M4] / nm;
-    o.q = a[tnmc::ACC_Q] / nq; o.q_abs = a[tnmc::ACC_QABS] / nq; o.q2 = a[tnmc::ACC_Q2] / nq; o.q4 = a[tnmc::ACC_Q4] / nq;
-  }
+  for (int k = 0; k < c->n_real; ++k) tnmc::obs_from_acc(&acc[(size_t)k * tnmc::ACC_SLOTS], cl[k], &out_host[k]);
   return TNMC_OK;
 }
 
@@ -480,12 +548,15 @@ tnmc_status tnmc_reset_chains(tnmc_ctx* c) {
 tnmc_status tnmc_destroy(tnmc_ctx* c) {
   if (!c) return TNMC_OK;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
-  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->allocs) {
+    if (c->async_alloc) cudaFreeAsync(p, c->stream); else cudaFree(p);
+  }
   if (c->h_stage) {
-    cudaFreeHost(c->h_stage);
+    tnmc::pinned_put(c->h_stage, (size_t)32 * c->cap * tnmc_ctx::kStageSlots);
     for (int s = 0; s < tnmc_ctx::kStageSlots; ++s) if (c->stage_ev[s]) cudaEventDestroy(c->stage_ev[s]);
   }
   c->allocs.clear();
+  c->alloc_sizes.clear();
   delete c;
   return TNMC_OK;
 }
@@ -509,6 +580,26 @@ tnmc_status tnmc_build_stats(tnmc_ctx* c, int64_t* out_host) {
 }
 
 int64_t tnmc_launch_count(const tnmc_ctx* c) { return c ? c->launches : 0; }
+
+size_t tnmc_device_bytes(const tnmc_ctx* c) {
+  if (!c) return 0;
+  size_t b = 0;
+  for (size_t s : c->alloc_sizes) b += s;
+  return b;
+}
+
+size_t tnmc_estimate_device_bytes(int L, int n_real, int chi, const tnmc_opts* opts, int n_max) {
+  if (L < 2 || n_real < 1 || !opts || n_max < 0 || round_chi(chi) == 0) return 0;
+  if (opts->n_chains < 1 || opts->n_chains > 8) return 0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;  // without a device: the GB300 count, for planning on a host
+  }
+  return ctx_sizes(L, n_real, round_chi(chi), opts->precision, opts->n_chains, sms).total() +
+         (n_max > 0 ? props_bytes(L, n_real, opts->n_chains, n_max) : 0);
+}
 
 tnmc_status tnmc_copy_env(tnmc_ctx* c, int real, int row, double* tiles_host, int32_t* dims_host, double* lam_host) {
   if (!c) return fail(nullptr, TNMC_ERR_ARG, "NULL context");
@@ -547,3 +638,108 @@ tnmc_status tnmc_copy_env(tnmc_ctx* c, int real, int row, double* tiles_host, in
 }
 
 }  // extern "C"
+
+namespace tnmc {
+
+// Pinned host blocks are kept for reuse instead of being returned with cudaFreeHost, which
+// may synchronise the device; the cache is bounded by the largest set of contexts alive at once.
+namespace {
+std::mutex g_pinned_mu;
+std::multimap<size_t, void*> g_pinned_free;
+}  // namespace
+
+void* pinned_get(size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto it = g_pinned_free.find(bytes);
+    if (it != g_pinned_free.end()) {
+      void* p = it->second;
+      g_pinned_free.erase(it);
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return p;
+}
+
+void pinned_put(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free.emplace(bytes, p);
+}
+
+void obs_from_acc(const double* a, int64_t clamps, tnmc_obs* out) {
+  tnmc_obs& o = *out;
+  std::memset(&o, 0, sizeof(o));
+  o.n_prop = (int64_t)llround(a[ACC_NPROP]);
+  o.n_acc = (int64_t)llround(a[ACC_NACC]);
+  o.n_meas = (int64_t)llround(a[ACC_NMEAS]);
+  o.n_meas_q = (int64_t)llround(a[ACC_NMEASQ]);
+  o.clamps = clamps;
+  const double nm = a[ACC_NMEAS] > 0 ? a[ACC_NMEAS] : 1.0;
+  const double nq = a[ACC_NMEASQ] > 0 ? a[ACC_NMEASQ] : 1.0;
+  o.E = a[ACC_E] / nm; o.E2 = a[ACC_E2] / nm; o.m_abs = a[ACC_MABS] / nm;
+  o.m2 = a[ACC_M2] / nm; o.m4 = a[ACC_M4] / nm;
+  o.q = a[ACC_Q] / nq; o.q_abs = a[ACC_QABS] / nq; o.q2 = a[ACC_Q2] / nq; o.q4 = a[ACC_Q4] / nq;
+}
+
+// A new batch on a pooled context (used by the request server): n_active <= capacity
+// realizations, each with its own seed, inverse temperature, bond probability and number of
+// proposals per chain; couplings are generated on the device; all asynchronous.
+tnmc_status ctx_begin_batch(tnmc_ctx* c, int n_active, const uint64_t* seeds, const double* betas,
+                            const double* ps, const int* nlimits) {
+  if (!c || n_active < 1 || n_active > c->cap) return fail(c, TNMC_ERR_ARG, "batch size outside the capacity");
+  for (int k = 0; k < n_active; ++k)
+    if (!(ps[k] >= 0.0 && ps[k] <= 1.0) || nlimits[k] < 1) return fail(c, TNMC_ERR_ARG, "bad p or n");
+  c->n_real = n_active;
+  tnmc_status s = stage_small_inputs(c, betas, seeds, ps, nlimits);
+  if (s) return s;
+  cudaError_t e = launch_couplings_pvec(c->L, c->n_real, c->seeds, c->pvec, c->J, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "couplings launch");
+  ++c->launches;
+  c->env_built = false;
+  c->use_nlimit = true;
+  const size_t chains = (size_t)c->n_real * c->n_chains;
+  e = cudaMemsetAsync(c->have_state, 0, sizeof(int) * chains, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(double) * (size_t)c->n_real * ACC_SLOTS, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->clamps, 0, sizeof(int64_t) * c->n_real, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reset");
+  c->have_props = false;
+  return TNMC_OK;
+}
+
+// Queue the device-to-host copies of a batch's results into the caller's pinned buffers
+// (acc: n_real x ACC_SLOTS, clamps, logz: n_real, stats: 4 n_real, status: 1).
+tnmc_status ctx_enqueue_readback(tnmc_ctx* c, double* acc_h, int64_t* clamps_h, double* logz_h,
+                                 long long* stats_h, unsigned* status_h) {
+  const size_t R = (size_t)c->n_real;
+  cudaError_t e = cudaMemcpyAsync(acc_h, c->acc, sizeof(double) * R * ACC_SLOTS, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(clamps_h, c->clamps, sizeof(int64_t) * R, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(logz_h, c->logz, sizeof(double) * R, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stats_h, c->stats, sizeof(long long) * 4 * R, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(status_h, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "result copy");
+  return TNMC_OK;
+}
+
+int ctx_capacity(const tnmc_ctx* c) { return c->cap; }
+
+cudaStream_t ctx_stream(const tnmc_ctx* c) { return c->stream; }
+
+void ctx_set_stream(tnmc_ctx* c, cudaStream_t st) { c->stream = st; }
+
+void ctx_release(tnmc_ctx* c, cudaStream_t st) {
+  if (!c) return;
+  for (void* p : c->allocs) {
+    if (c->async_alloc) cudaFreeAsync(p, st); else cudaFree(p);
+  }
+  if (c->h_stage) {
+    tnmc::pinned_put(c->h_stage, (size_t)32 * c->cap * tnmc_ctx::kStageSlots);
+    for (int k = 0; k < tnmc_ctx::kStageSlots; ++k) if (c->stage_ev[k]) cudaEventDestroy(c->stage_ev[k]);
+  }
+  delete c;
+}
+
+}  // namespace tnmc

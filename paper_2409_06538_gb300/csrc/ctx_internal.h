@@ -1,0 +1,41 @@
+// Library-internal entry points on a TNMC context, used by the request server (server.cu) to
+// run batches asynchronously on pooled contexts.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "../../include/tnmc.h"
+
+namespace tnmc {
+
+// Fill a tnmc_obs from one realization's accumulator row (ACC_SLOTS doubles) and clamp count.
+void obs_from_acc(const double* acc_row, int64_t clamps, tnmc_obs* out);
+
+// Start a batch of n_active <= capacity realizations with their own seeds, inverse
+// temperatures, antiferromagnetic-bond probabilities and total proposals per chain:
+// generates the couplings on the device and resets the chains.  Asynchronous on the
+// context's stream; the host arrays may be reused on return.
+tnmc_status ctx_begin_batch(tnmc_ctx* c, int n_active, const uint64_t* seeds, const double* betas,
+                            const double* ps, const int* nlimits);
+
+// Queue copies of the batch results into pinned host memory: accumulators (n_active x
+// ACC_SLOTS), clamp counts and log Z (n_active), build statistics (4 n_active), status word.
+tnmc_status ctx_enqueue_readback(tnmc_ctx* c, double* acc_h, int64_t* clamps_h, double* logz_h,
+                                 long long* stats_h, unsigned* status_h);
+
+int ctx_capacity(const tnmc_ctx* c);
+
+// Pinned host memory from a process-wide cache (never handed back with cudaFreeHost while
+// the process runs, so that releasing it cannot synchronise the device).
+void* pinned_get(size_t bytes);
+void pinned_put(void* p, size_t bytes);
+cudaStream_t ctx_stream(const tnmc_ctx* c);
+
+// Move a context to another stream.  The caller orders the switch: all work queued on the
+// old stream must have completed (or be ordered before the new stream's work).
+void ctx_set_stream(tnmc_ctx* c, cudaStream_t st);
+
+// Free a context whose work has all completed, queueing the device frees on `st` and
+// waiting for nothing (tnmc_destroy first synchronises the context's stream).
+void ctx_release(tnmc_ctx* c, cudaStream_t st);
+
+}  // namespace tnmc

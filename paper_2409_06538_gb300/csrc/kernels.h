@@ -82,12 +82,16 @@ struct AcceptArgs {
   uint32_t* cur_spins;             // [real][chain][words]
   double* acc;                     // [real][16] accumulators
   int* cur_idx;                    // [real][chain][k] scratch: current state after step k
+  const int* nlimit;               // [real] proposals per chain a realization uses in all, counted
+                                   // from step 0; later steps are skipped (nullable: no limit)
   unsigned* status;
 };
 cudaError_t launch_accept(const AcceptArgs& a, cudaStream_t st);
 
 cudaError_t launch_couplings(int L, int n_real, const uint64_t* seeds_dev, double p, int8_t* out,
                              cudaStream_t st);
+cudaError_t launch_couplings_pvec(int L, int n_real, const uint64_t* seeds_dev, const double* p_dev, int8_t* out,
+                                  cudaStream_t st);
 cudaError_t launch_unpack(const uint32_t* packed, int words, int N, int64_t n_cfg, int8_t* out,
                           cudaStream_t st);
 

@@ -36,6 +36,13 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
   __shared__ double red[32];
   __shared__ double nacc_s[8];
   int* cur = a.cur_idx + (size_t)real * nc * n;
+  // proposals of this call that the realization uses: all n, or what is left of its own
+  // per-realization total after step0 (the rest is skipped as if never drawn)
+  int lim = n;
+  if (a.nlimit) {
+    const long long left = (long long)a.nlimit[real] - (long long)a.step0;
+    lim = left <= 0 ? 0 : (left < n ? (int)left : n);
+  }
 
   if (tid < nc) {
     const int ch = tid;
@@ -47,6 +54,11 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
     int c = -1;
     int64_t nacc = 0;
     for (int k = 0; k < n; ++k) {
+      if (k >= lim) {                       // beyond this realization's own proposal count
+        if (a.accepted) a.accepted[base + k] = 0;
+        cur[(size_t)ch * n + k] = c;
+        continue;
+      }
       const double E = (double)a.energy[base + k], lq = a.logq[base + k];
       bool ok;
       if (!have) {
@@ -68,8 +80,10 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
   // ---- phase 2: observables
   const double invN = 1.0 / (double)N;
   double sE = 0, sE2 = 0, sMa = 0, sM2 = 0, sM4 = 0, nm = 0;
-  for (int idx = tid; idx < nc * n; idx += blockDim.x) {
-    const int ch = idx / n, k = idx % n;
+  // items are dealt to threads by (chain, step < lim), so the sums depend only on the
+  // realization's own proposals, whatever the call's n
+  for (int idx = tid; idx < nc * lim; idx += blockDim.x) {
+    const int ch = idx / lim, k = idx % lim;
     if ((int64_t)(a.step0 + k) < (int64_t)a.n_therm) continue;
     const int c = cur[(size_t)ch * n + k];
     const size_t sidx = (size_t)real * nc + ch;
@@ -82,6 +96,7 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
   double sq = 0, sqa = 0, sq2 = 0, sq4 = 0, nq = 0;
   if (nc >= 2) {
     for (int k = tid; k < n; k += blockDim.x) {
+      if (k >= lim) continue;
       if ((int64_t)(a.step0 + k) < (int64_t)a.n_therm) continue;
       const int c0 = cur[k], c1 = cur[(size_t)n + k];
       const size_t s0 = (size_t)real * nc + 0, s1 = (size_t)real * nc + 1;
@@ -103,7 +118,7 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
     double* acc = a.acc + (size_t)real * ACC_SLOTS;
     double na = 0;
     for (int ch = 0; ch < nc && ch < 8; ++ch) na += nacc_s[ch];
-    acc[ACC_NPROP] += (double)nc * n;
+    acc[ACC_NPROP] += (double)nc * lim;
     acc[ACC_NACC] += na;
     acc[ACC_NMEAS] += nm;
     acc[ACC_NMEASQ] += nq;
@@ -134,7 +149,7 @@ cudaError_t launch_accept(const AcceptArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-__global__ void couplings_kernel(int L, int n_real, const uint64_t* seeds, double p, int8_t* out) {
+__global__ void couplings_kernel(int L, int n_real, const uint64_t* seeds, double p, const double* pvec, int8_t* out) {
   const int64_t nb = 2ll * L * (L - 1);
   const int64_t total = nb * n_real;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
@@ -142,7 +157,7 @@ __global__ void couplings_kernel(int L, int n_real, const uint64_t* seeds, doubl
     const int real = (int)(i / nb);
     const uint32_t b = (uint32_t)(i % nb);
     const double u = uniform(seeds[real], b, 0u, 0u, PURPOSE_BOND);
-    out[i] = (u < p) ? (int8_t)-1 : (int8_t)1;
+    out[i] = (u < (pvec ? pvec[real] : p)) ? (int8_t)-1 : (int8_t)1;
   }
 }
 
@@ -151,7 +166,16 @@ cudaError_t launch_couplings(int L, int n_real, const uint64_t* seeds_dev, doubl
   const int64_t total = 2ll * L * (L - 1) * n_real;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 65535) blocks = 65535;
-  couplings_kernel<<<(unsigned)blocks, 256, 0, st>>>(L, n_real, seeds_dev, p, out);
+  couplings_kernel<<<(unsigned)blocks, 256, 0, st>>>(L, n_real, seeds_dev, p, nullptr, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_couplings_pvec(int L, int n_real, const uint64_t* seeds_dev, const double* p_dev, int8_t* out,
+                                  cudaStream_t st) {
+  const int64_t total = 2ll * L * (L - 1) * n_real;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  couplings_kernel<<<(unsigned)blocks, 256, 0, st>>>(L, n_real, seeds_dev, 0.0, p_dev, out);
   return cudaGetLastError();
 }
 
