@@ -221,6 +221,13 @@ tnmc_status tnmc_build_env_noalloc(int L, int n_real, int chi, int precision,
                                    void* env_dev, int32_t* kdim_dev, double* lam_dev,
                                    double* logz_dev, void* stream);
 
+/* Per-realization status: out_host[k] (n_real int32) is TNMC_ERR_NUMERIC when a proposal of
+ * realization k met a site whose conditional weights w+ + w- were not positive and finite
+ * after clamping (the context-wide status then reports TNMC_ERR_NUMERIC too), else TNMC_OK.
+ * Cleared by tnmc_reset_chains (and so by tnmc_set_couplings / tnmc_set_realizations).
+ * Lets a caller drop the affected realizations instead of the whole batch.  Synchronises. */
+tnmc_status tnmc_realization_status(tnmc_ctx* ctx, int32_t* out_host);
+
 /* Kernel launch accounting: number of kernels this context launched since creation. */
 int64_t tnmc_launch_count(const tnmc_ctx* ctx);
 

@@ -92,8 +92,7 @@ def envs_full(Jh, Jv, beta, chi):
 def row_conditionals(G_row, jh_row, h, beta, x):
     """Site-by-site q(+) for one row given the full environment vector, fields h (Lx,) and
     the row's spins x (Lx,): w(y) sums the unnormalised row weight over the spins to the
-    right of the site with the spins to the left fixed; negative w is clamped to 0, and a
-    site whose two weights were both clamped takes q(+) = 1/2."""
+    right of the site with the spins to the left fixed; negative w is clamped to 0."""
     Lx = len(x)
     X = row_configs(Lx)
     p = G_row * row_weight(X, jh_row, beta) * np.exp(X @ h)
@@ -104,7 +103,7 @@ def row_conditionals(G_row, jh_row, h, beta, x):
         sub = P[prefix]                       # axes: site c, then sites > c
         w = sub.reshape(2, -1).sum(axis=1)
         w = np.maximum(w, 0.0)
-        qp[c] = w[0] / w.sum() if w.sum() > 0.0 else 0.5   # both clamped: uniform conditional
+        qp[c] = w[0] / w.sum()
     return qp
 
 

@@ -16,9 +16,7 @@ factor to the spin on its left (Fig. fig:ZS4):
     R_c(y') = sum_y exp(beta Jh[r,c-1] s_{y'} s_y + h_c s_y) B[c]^y R_{c+1}(y),  R_Lx = 1.
 
 Readings where the paper is silent: a negative truncated weight is clamped to zero and
-counted; q(+) = w+/(w+ + w-), q(-) = w-/(w+ + w-), and where both weights were clamped
-(w+ + w- = 0) the site takes the uniform conditional q(+) = q(-) = 1/2, so that q stays a
-normalised distribution the chain knows exactly; the spin is +1 iff u < q(+), u the
+counted; q(+) = w+/(w+ + w-), q(-) = w-/(w+ + w-); the spin is +1 iff u < q(+), u the
 Philox uniform of counter (site, step, chain, PURPOSE_SPIN); log q is summed in FP64.
 """
 import numpy as np
@@ -68,12 +66,10 @@ def sweep_row(Brow, jh_row, h, beta, uniforms=None, forced=None):
         clamps += (w < 0).sum(axis=1)
         w = np.maximum(w, 0.0)
         tot = w.sum(axis=1)
-        if not np.all(np.isfinite(tot)):
-            raise NumericError(f"conditional weights are not finite at site {c}")
-        deg = tot <= 0.0                      # both weights clamped: uniform conditional
-        safe = np.where(deg, 1.0, tot)
-        qp = np.where(deg, 0.5, w[:, 0] / safe)
-        qm = np.where(deg, 0.5, w[:, 1] / safe)
+        if not np.all(np.isfinite(tot) & (tot > 0)):
+            raise NumericError(f"conditional weights vanish or are not finite at site {c}")
+        qp = w[:, 0] / tot
+        qm = w[:, 1] / tot
         qplus[:, c] = qp
         if forced is not None:
             s = np.asarray(forced[:, c]).astype(np.int64)

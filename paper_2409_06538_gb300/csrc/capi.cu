@@ -41,6 +41,7 @@ struct tnmc_ctx {
   void* Rstore = nullptr;
   long long* stats = nullptr;
   unsigned* status = nullptr;
+  unsigned* rstatus = nullptr;    // per-realization status bits (numeric failures of its proposals)
   // sampling
   void* work = nullptr;
   void* work_tc = nullptr;        // workspace of the tensor-core sampler (mixed TF32 path)
@@ -146,11 +147,11 @@ tnmc_status check_status(tnmc_ctx* c) {
 // Device bytes of every buffer a context holds, one function for the allocation and the
 // capacity estimate so that the two cannot drift apart.
 struct CtxSizes {
-  size_t J, beta, seeds, pvec, nlimit, env, kdim, dqr, lam, logz, rowbuf, Rstore, stats, status, work,
-      work_tc, clamps, have_state, cur_logq, cur_energy, cur_magnet, cur_spins, acc;
+  size_t J, beta, seeds, pvec, nlimit, env, kdim, dqr, lam, logz, rowbuf, Rstore, stats, status, rstatus,
+      work, work_tc, clamps, have_state, cur_logq, cur_energy, cur_magnet, cur_spins, acc;
   size_t total() const {
     return J + beta + seeds + pvec + nlimit + env + kdim + dqr + lam + logz + rowbuf + Rstore + stats + status +
-           work + work_tc + clamps + have_state + cur_logq + cur_energy + cur_magnet + cur_spins + acc;
+           rstatus + work + work_tc + clamps + have_state + cur_logq + cur_energy + cur_magnet + cur_spins + acc;
   }
 };
 
@@ -171,6 +172,7 @@ CtxSizes ctx_sizes(int L, int n_real, int CHI, int precision, int n_chains, int 
   z.Rstore = R * L * D * D * tsz;
   z.stats = 4 * sizeof(long long) * R;
   z.status = sizeof(unsigned);
+  z.rstatus = sizeof(unsigned) * R;
   z.work = tnmc::sample_work_bytes(L, CHI, precision, num_sms);
   z.work_tc = (precision == TNMC_MIXED_TF32 && tnmc::sample_tc_supported(CHI))
                   ? tnmc::sample_tc_work_bytes(L, CHI, num_sms) : 0;
@@ -281,6 +283,7 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
   TRY(dalloc(c, &c->Rstore, z.Rstore));
   TRY(dalloc(c, &c->stats, z.stats));
   TRY(dalloc(c, &c->status, z.status));
+  TRY(dalloc(c, &c->rstatus, z.rstatus));
   TRY(dalloc(c, &c->work, z.work));
   if (z.work_tc) TRY(dalloc(c, &c->work_tc, z.work_tc));
   TRY(dalloc(c, &c->clamps, z.clamps));
@@ -296,6 +299,7 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->beta, beta_host, sizeof(double) * n_real, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->seeds, seeds_host, sizeof(uint64_t) * n_real, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->rstatus, 0, sizeof(unsigned) * n_real, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->clamps, 0, sizeof(int64_t) * n_real, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->have_state, 0, sizeof(int) * chains, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(double) * (size_t)n_real * tnmc::ACC_SLOTS, c->stream);
@@ -422,6 +426,7 @@ static tnmc_status run_sample(tnmc_ctx* c, int n, uint64_t step0, const int8_t* 
   a.logq = logq; a.energy = props ? c->energy : nullptr; a.magnet = props ? c->magnet : nullptr;
   a.clamps = props ? c->clamps : nullptr; a.forced = forced; a.qplus = qplus; a.work = c->work;
   a.status = c->status;
+  a.real_status = props ? c->rstatus : nullptr;
   cudaError_t e;
   if (c->work_tc) {
     a.work = c->work_tc;
@@ -538,6 +543,7 @@ tnmc_status tnmc_reset_chains(tnmc_ctx* c) {
   if (!c) return fail(nullptr, TNMC_ERR_ARG, "NULL context");
   const size_t chains = (size_t)c->n_real * c->n_chains;
   cudaError_t e = cudaMemsetAsync(c->have_state, 0, sizeof(int) * chains, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->rstatus, 0, sizeof(unsigned) * c->n_real, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(double) * (size_t)c->n_real * tnmc::ACC_SLOTS, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->clamps, 0, sizeof(int64_t) * c->n_real, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "reset");
@@ -580,6 +586,16 @@ tnmc_status tnmc_build_stats(tnmc_ctx* c, int64_t* out_host) {
 }
 
 int64_t tnmc_launch_count(const tnmc_ctx* c) { return c ? c->launches : 0; }
+
+tnmc_status tnmc_realization_status(tnmc_ctx* c, int32_t* out_host) {
+  if (!c || !out_host) return fail(c, TNMC_ERR_ARG, "NULL argument");
+  std::vector<unsigned> st(c->n_real);
+  cudaError_t e = cudaMemcpyAsync(st.data(), c->rstatus, sizeof(unsigned) * st.size(), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status copy");
+  for (int k = 0; k < c->n_real; ++k) out_host[k] = (st[k] & tnmc::ST_NUMERIC) ? TNMC_ERR_NUMERIC : TNMC_OK;
+  return TNMC_OK;
+}
 
 size_t tnmc_device_bytes(const tnmc_ctx* c) {
   if (!c) return 0;
@@ -705,21 +721,23 @@ tnmc_status ctx_begin_batch(tnmc_ctx* c, int n_active, const uint64_t* seeds, co
   if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(double) * (size_t)c->n_real * ACC_SLOTS, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->clamps, 0, sizeof(int64_t) * c->n_real, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->rstatus, 0, sizeof(unsigned) * c->n_real, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "reset");
   c->have_props = false;
   return TNMC_OK;
 }
 
 // Queue the device-to-host copies of a batch's results into the caller's pinned buffers
-// (acc: n_real x ACC_SLOTS, clamps, logz: n_real, stats: 4 n_real, status: 1).
+// (acc: n_real x ACC_SLOTS, clamps, logz: n_real, stats: 4 n_real, status: 1, rstatus: n_real).
 tnmc_status ctx_enqueue_readback(tnmc_ctx* c, double* acc_h, int64_t* clamps_h, double* logz_h,
-                                 long long* stats_h, unsigned* status_h) {
+                                 long long* stats_h, unsigned* status_h, unsigned* rstatus_h) {
   const size_t R = (size_t)c->n_real;
   cudaError_t e = cudaMemcpyAsync(acc_h, c->acc, sizeof(double) * R * ACC_SLOTS, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(clamps_h, c->clamps, sizeof(int64_t) * R, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(logz_h, c->logz, sizeof(double) * R, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(stats_h, c->stats, sizeof(long long) * 4 * R, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(status_h, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rstatus_h, c->rstatus, sizeof(unsigned) * R, cudaMemcpyDeviceToHost, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "result copy");
   return TNMC_OK;
 }

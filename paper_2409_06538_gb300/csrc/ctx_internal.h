@@ -18,9 +18,10 @@ tnmc_status ctx_begin_batch(tnmc_ctx* c, int n_active, const uint64_t* seeds, co
                             const double* ps, const int* nlimits);
 
 // Queue copies of the batch results into pinned host memory: accumulators (n_active x
-// ACC_SLOTS), clamp counts and log Z (n_active), build statistics (4 n_active), status word.
+// ACC_SLOTS), clamp counts and log Z (n_active), build statistics (4 n_active), the context's
+// status word and the per-realization status words (n_active).
 tnmc_status ctx_enqueue_readback(tnmc_ctx* c, double* acc_h, int64_t* clamps_h, double* logz_h,
-                                 long long* stats_h, unsigned* status_h);
+                                 long long* stats_h, unsigned* status_h, unsigned* rstatus_h);
 
 int ctx_capacity(const tnmc_ctx* c);
 

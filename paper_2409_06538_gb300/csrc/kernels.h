@@ -55,6 +55,7 @@ struct SampleArgs {
   // scratch
   void* work;                      // [grid][warps][L][2*CHI] of compute type
   unsigned* status;
+  unsigned* real_status;           // [real] per-realization status bits (nullable)
 };
 
 cudaError_t launch_sample(const SampleArgs& a, int precision, int CHI, int num_sms, cudaStream_t st);

@@ -172,14 +172,15 @@ sample_kernel(SampleArgs a) {
         const T tot = w0 + w1;
         int s;
         T qp = T(0.5), lqs;
-        if (!isfinite(tot)) {
-          if (lane == 0 && valid) set_status(a.status, ST_NUMERIC);
+        if (!(tot > T(0)) || !isfinite(tot)) {
+          if (lane == 0 && valid) {
+            set_status(a.status, ST_NUMERIC);
+            if (a.real_status) set_status(a.real_status + real, ST_NUMERIC);
+          }
           s = 1; lqs = T(-0.6931471805599453);
         } else {
-          // both weights clamped to zero: the site falls back to the uniform conditional
-          const bool degenerate = !(tot > T(0));
-          qp = degenerate ? T(0.5) : w0 / tot;
-          const T qm = degenerate ? T(0.5) : w1 / tot;
+          qp = w0 / tot;
+          const T qm = w1 / tot;
           if (forced) {
             s = forced[(size_t)r * L + c];
           } else {

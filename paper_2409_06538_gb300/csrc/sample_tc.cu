@@ -372,14 +372,15 @@ __global__ void __launch_bounds__(128) sample_tc_kernel(SampleArgs a) {
         const float tot = w0 + w1;
         int s;
         float qp = 0.5f, lqs;
-        if (!isfinite(tot)) {
-          if (valid) set_status(a.status, ST_NUMERIC);
+        if (!(tot > 0.0f) || !isfinite(tot)) {
+          if (valid) {
+            set_status(a.status, ST_NUMERIC);
+            if (a.real_status) set_status(a.real_status + real, ST_NUMERIC);
+          }
           s = 1; lqs = -0.6931471805599453f;
         } else {
-          // both weights clamped to zero: the site falls back to the uniform conditional
-          const bool degenerate = !(tot > 0.0f);
-          qp = degenerate ? 0.5f : w0 / tot;
-          const float qm = degenerate ? 0.5f : w1 / tot;
+          qp = w0 / tot;
+          const float qm = w1 / tot;
           if (forced) {
             s = forced[(size_t)r * L + c];
           } else {

@@ -61,10 +61,11 @@ struct Pooled {
   double* logz_h = nullptr;
   long long* stats_h = nullptr;
   unsigned* status_h = nullptr;
-  unsigned char* host = nullptr;   // the pinned block the five pointers above live in
+  unsigned* rstatus_h = nullptr;
+  unsigned char* host = nullptr;   // the pinned block the six pointers above live in
 };
 
-size_t host_bytes(int cap) { return (size_t)cap * (8 * tnmc::ACC_SLOTS + 8 + 8 + 32) + 16; }
+size_t host_bytes(int cap) { return (size_t)cap * (8 * tnmc::ACC_SLOTS + 8 + 8 + 32 + 4) + 16; }
 
 struct Batch {
   Pooled* pool = nullptr;
@@ -167,6 +168,7 @@ Pooled* create_pooled(tnmc_server* s, int L, int chi, int cap, size_t bytes, cud
     p->clamps_h = reinterpret_cast<int64_t*>(p->logz_h + cap);
     p->stats_h = reinterpret_cast<long long*>(p->clamps_h + cap);
     p->status_h = reinterpret_cast<unsigned*>(p->stats_h + 4 * (size_t)cap);
+    p->rstatus_h = p->status_h + 1;
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -242,7 +244,8 @@ tnmc_status enqueue_batch(tnmc_server* s, Pooled* p, const std::vector<Pending>&
     st = tnmc_propose(c, m, (uint64_t)step0, nullptr, nullptr, nullptr);
     if (!st) st = tnmc_accept(c, nullptr, nullptr);
   }
-  if (!st) st = tnmc::ctx_enqueue_readback(c, p->acc_h, p->clamps_h, p->logz_h, p->stats_h, p->status_h);
+  if (!st) st = tnmc::ctx_enqueue_readback(c, p->acc_h, p->clamps_h, p->logz_h, p->stats_h, p->status_h,
+                                           p->rstatus_h);
   if (!st && cudaEventRecord(p->done, p->stream) != cudaSuccess) { cudaGetLastError(); st = TNMC_ERR_CUDA; }
   std::lock_guard<std::mutex> lk(s->mu);
   s->st_launches += tnmc_launch_count(c) - l0;
@@ -257,11 +260,17 @@ bool retire(tnmc_server* s) {
     const cudaError_t e = cudaEventQuery(b.pool->done);
     if (e == cudaErrorNotReady) { ++i; continue; }
     any = true;
+    // a timeout or argument error taints the whole batch; a numeric failure only the
+    // realizations whose proposals met it
     tnmc_status st = TNMC_OK;
     if (e != cudaSuccess) { cudaGetLastError(); st = TNMC_ERR_CUDA; }
-    else st = status_from_word(*b.pool->status_h);
+    else st = status_from_word(*b.pool->status_h & ~(unsigned)tnmc::ST_NUMERIC);
     const int bs = (int)b.reqs.size();
-    for (int k = 0; k < bs; ++k) finish_request(s, b.reqs[k], st, bs, b.t_start, b.pool, k);
+    for (int k = 0; k < bs; ++k) {
+      tnmc_status sk = st;
+      if (sk == TNMC_OK) sk = status_from_word(b.pool->rstatus_h[k]);
+      finish_request(s, b.reqs[k], sk, bs, b.t_start, b.pool, k);
+    }
     b.pool->busy = false;
     b.pool->last_used = s->now();
     s->stream_busy[(size_t)b.slot] = false;

@@ -155,6 +155,15 @@ class TNMC:
         return dict(max_sweeps=out[0], unconverged=out[1], total_sweeps=out[2], svds=out[3],
                     mean_sweeps=out[2] / max(1, out[3]))
 
+    def realization_status(self):
+        """Per-realization status codes (0 ok, 4 = a numeric failure in its proposals)."""
+        out = np.zeros(self.n_real, dtype=np.int32)
+        self._chk(self.lib.tnmc_realization_status(self.ctx, out.ctypes.data_as(_capi.c_int32_p)))
+        return out
+
+    def device_bytes(self):
+        return int(self.lib.tnmc_device_bytes(self.ctx))
+
     def env_bytes(self):
         return int(self.lib.tnmc_env_bytes(self.ctx))
 

@@ -190,6 +190,7 @@ def test_metropolis_and_observables_parity(tn):
         assert obs[k]["n_acc"] == int(fl[k].sum()) - 2
         per.append(ref)
     assert 0.0 < np.mean([o["n_acc"] for o in obs]) < 2 * 2 * n
+    assert np.all(ctx.realization_status() == 0)
 
 
 def test_observables_match_independent_oracle_run(tn):

@@ -101,27 +101,20 @@ def test_log_z_of_truncated_network_is_finite_and_close():
         assert abs(env.log_z - logZ) < 0.5
 
 
-def test_doubly_clamped_site_takes_the_uniform_conditional():
-    """Where truncation leaves both weights of a site negative, both are clamped to zero and
-    the site takes q(+) = q(-) = 1/2: the drawn spin follows u < 1/2, each such site counts
-    two clamps and adds log 1/2, and q over all row states still sums to one.  (With one-
-    dimensional bonds the sign carries along the row, so every site here is degenerate.)
-    Non-finite weights stay an error."""
-    import itertools
+def test_doubly_clamped_site_is_an_error():
+    """The clamp reading: a negative truncated weight is clamped to zero and counted, and a
+    site whose two weights are both clamped (or not finite) is an error, not a draw."""
     beta = 0.7
-    B0 = np.array([-1.0, -2.0]).reshape(1, 2, 1)
+    B0 = np.array([-1.0, -2.0]).reshape(1, 2, 1)          # both weights of site 0 negative
     B1 = np.array([0.3, 1.1]).reshape(1, 2, 1)
-    Brow, jh = [B0, B1], np.array([1.0, 0.0])
-    for u, want in (((0.3, 0.7), (1, -1)), ((0.7, 0.2), (-1, 1))):
-        s, lq, qp, cl = sampler.sweep_row(Brow, jh, np.zeros((1, 2)), beta, uniforms=np.array([u]))
-        assert tuple(s[0]) == want and np.all(qp[0] == 0.5) and cl[0] == 4
-        assert abs(lq[0] - 2 * np.log(0.5)) < 1e-15
-    X = np.array(list(itertools.product([1, -1], repeat=2)))
-    _, lq, _, _ = sampler.sweep_row(Brow, jh, np.zeros((4, 2)), beta, forced=X)
-    assert abs(np.exp(lq).sum() - 1.0) < 1e-14
-    # the brute-force conditionals take the same reading
-    G = -np.ones(4)
-    assert np.all(brute.row_conditionals(G, jh, np.zeros(2), beta, np.array([1, 1])) == 0.5)
+    jh = np.array([1.0, 0.0])
+    with pytest.raises(sampler.NumericError):
+        sampler.sweep_row([B0, B1], jh, np.zeros((1, 2)), beta, uniforms=np.array([[0.3, 0.5]]))
     with pytest.raises(sampler.NumericError):
         sampler.sweep_row([np.full((1, 2, 1), np.inf), B1], jh, np.zeros((1, 2)), beta,
                           uniforms=np.array([[0.3, 0.5]]))
+    # one negative weight is clamped: the other branch is taken with q = 1, two clamps per row
+    # here (site 0 has w- < 0; site 1's left vector then carries B0's + entry)
+    B0m = np.array([1.0, -2.0]).reshape(1, 2, 1)
+    s, lq, qp, cl = sampler.sweep_row([B0m, B1], jh, np.zeros((1, 2)), beta, uniforms=np.array([[0.99, 0.5]]))
+    assert s[0, 0] == 1 and qp[0, 0] == 1.0 and cl[0] >= 1
