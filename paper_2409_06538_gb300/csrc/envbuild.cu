@@ -149,7 +149,7 @@ template <int CHI> struct Pair {
 };
 
 template <typename T, typename TE, int CHI>
-__global__ void __launch_bounds__(EnvCfg<CHI>::NT)
+__global__ void __launch_bounds__(EnvCfg<CHI>::NT, 2)
 env_build_kernel(EnvBuildArgs<T, TE> args) {
   using C = EnvCfg<CHI>;
   constexpr int D = C::D, NWARP = C::NWARP, NT = C::NT, TILE = C::TILE;
@@ -491,7 +491,11 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
           for (int e = tid; e < PAD * n; e += NT) Yc[(size_t)(e / PAD) * DP + D + e % PAD] = T(0);
         }
       }
-      for (int e = tid; e < DP * n; e += NT) { const int i = e % DP, j = e / DP; Vc[e] = (i == j) ? T(1) : T(0); }
+      // the Jacobi runs on npad = n rounded up to 8 columns (blocks of 4, an even number of
+      // blocks); columns n..npad-1 of Y are zero and never rotate
+      const int npad = (n + 7) & ~7;
+      for (int e = tid; e < DP * npad; e += NT) { const int i = e % DP, j = e / DP; Vc[e] = (i == j) ? T(1) : T(0); }
+      for (int e = tid; e < DP * (npad - n); e += NT) Yc[(size_t)n * DP + e] = T(0);
       fro = warp_sum(fro);
       if (lane == 0) red[warp] = fro;
       if (tid == 0) { rot[0] = 0; rot[1] = 0; rot[2] = 0; }
@@ -506,66 +510,88 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       // R_{c-1} streams in while the SVD runs (Rc is not read again at this site)
       if (c > 1) prefetch_async(Rc, Rstore + (size_t)(c - 1) * D * D, D * D * (int)sizeof(T), tid, NT);
       const T tol = jacobi_tol<T, D>();
-      // One-sided Jacobi: the n/2 pairs of a round are disjoint; 8 lanes per pair, each lane
-      // holding DP/8 rows of both columns in 16-byte vectors; the three dot products of a
-      // pair are reduced together over the 8 lanes.
+      // One-sided Jacobi in a block-cyclic order.  The npad columns form NB = npad/4 blocks of
+      // four; in each block-round (a round-robin over blocks) warp wj owns one block pair and
+      // its four 8-lane groups orthogonalise the 16 cross pairs in four sub-rounds (group i:
+      // column i of block A against column (i+t) mod 4 of block B), and in the first
+      // block-round also the six pairs inside each of its two blocks (three sub-rounds).  Every
+      // pair of columns meets once per sweep; the columns a warp touches in a block-round are
+      // its own, so sub-rounds are ordered by __syncwarp and only block-rounds need the
+      // CTA-wide barrier (NB-1 per sweep instead of npad-1).  8 lanes per pair, each lane
+      // holding DP/8 rows of both columns in 16-byte vectors; the three dot products of a pair
+      // are reduced together over the 8 lanes.
       constexpr int NJ = 8 * CHI;
       constexpr int VEC = JStride<T, CHI>::VEC;
       constexpr int NV = DP / (8 * VEC);
       using V16 = typename Vec16<T>::type;
       int sweep = 0;
       if (tid < NJ) {
-        const int w = tid >> 3, li = tid & 7;
-        const bool active = w < n / 2;
-        const int m1 = n - 1;
+        const int wj = tid >> 5, grp = (tid >> 3) & 3, li = tid & 7;
+        const int NB = npad / 4, mb = NB - 1;
+        const bool wact = wj < NB / 2;
+        auto jpair = [&](int p, int q) {
+          V16* yp = reinterpret_cast<V16*>(Yc + (size_t)p * DP);
+          V16* yq = reinterpret_cast<V16*>(Yc + (size_t)q * DP);
+          V16* vp = reinterpret_cast<V16*>(Vc + (size_t)p * DP);
+          V16* vq = reinterpret_cast<V16*>(Vc + (size_t)q * DP);
+          V16 up[NV], uq[NV], wp[NV], wq[NV];
+          T g = 0, a = 0, b = 0;
+#pragma unroll
+          for (int k = 0; k < NV; ++k) {
+            up[k] = yp[li + 8 * k];
+            uq[k] = yq[li + 8 * k];
+            wp[k] = vp[li + 8 * k];     // issued early: their latency overlaps the reductions
+            wq[k] = vq[li + 8 * k];
+          }
+#pragma unroll
+          for (int k = 0; k < NV; ++k) {
+            g += dot16(up[k], uq[k]);
+            a += dot16(up[k], up[k]);
+            b += dot16(uq[k], uq[k]);
+          }
+          g = group8_sum(g); a = group8_sum(a); b = group8_sum(b);
+          if (a > tinyY && b > tinyY && g * g > tol * tol * a * b) {
+            T cs, sn;
+            rotation_from_gram(a, b, g, cs, sn);
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+              rot16(up[k], uq[k], cs, sn);
+              rot16(wp[k], wq[k], cs, sn);
+              yp[li + 8 * k] = up[k];
+              yq[li + 8 * k] = uq[k];
+              vp[li + 8 * k] = wp[k];
+              vq[li + 8 * k] = wq[k];
+            }
+            if (li == 0) rot[sweep % 3] = 1;
+          }
+        };
         for (; sweep < JacobiTol<T>::maxsw; ++sweep) {
           // clear the flag of sweep+1; the slot was last read at the end of sweep-2, and every
           // thread has passed a barrier of sweep-1 since (a two-slot ring would let a slow
           // thread read a flag that was already cleared and leave the loop alone)
           if (tid == 0) rot[(sweep + 1) % 3] = 0;
-          // round-robin pair of slot w in round 0; each later round adds 1 (mod n-1) to
-          // both members, except that slot 0 keeps column n-1
-          int p = 0, q = 0;
-          if (active) Pair<CHI>::get(n, 0, w, p, q);
-          for (int rd = 0; rd < m1; ++rd) {
-            if (rd > 0 && active) {
-              if (w != 0) p = (p + 1 == m1) ? 0 : p + 1;
-              q = (q + 1 == m1) ? 0 : q + 1;
-            }
-            V16* yp = reinterpret_cast<V16*>(Yc + (size_t)p * DP);
-            V16* yq = reinterpret_cast<V16*>(Yc + (size_t)q * DP);
-            V16* vp = reinterpret_cast<V16*>(Vc + (size_t)p * DP);
-            V16* vq = reinterpret_cast<V16*>(Vc + (size_t)q * DP);
-            V16 up[NV], uq[NV], wp[NV], wq[NV];
-            T g = 0, a = 0, b = 0;
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-              up[k] = yp[li + 8 * k];
-              uq[k] = yq[li + 8 * k];
-              wp[k] = vp[li + 8 * k];     // issued early: their latency overlaps the reductions
-              wq[k] = vq[li + 8 * k];
-            }
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-              g += dot16(up[k], uq[k]);
-              a += dot16(up[k], up[k]);
-              b += dot16(uq[k], uq[k]);
-            }
-            g = group8_sum(g); a = group8_sum(a); b = group8_sum(b);
-            const bool do_rot = active && a > tinyY && b > tinyY && g * g > tol * tol * a * b;
-            if (do_rot) {
-              T cs, sn;
-              rotation_from_gram(a, b, g, cs, sn);
-#pragma unroll
-              for (int k = 0; k < NV; ++k) {
-                rot16(up[k], uq[k], cs, sn);
-                rot16(wp[k], wq[k], cs, sn);
-                yp[li + 8 * k] = up[k];
-                yq[li + 8 * k] = uq[k];
-                vp[li + 8 * k] = wp[k];
-                vq[li + 8 * k] = wq[k];
+          for (int br = 0; br < mb; ++br) {
+            if (wact) {       // warp-uniform: the shuffles of jpair need the whole warp
+              // block pair of slot wj (circle method: slot 0 keeps block NB-1)
+              const int bA = wj == 0 ? NB - 1 : (br + wj) % mb;
+              const int bB = wj == 0 ? br : (br - wj + mb) % mb;
+              if (br == 0) {
+                // pairs inside blocks A (groups 0, 1) and B (groups 2, 3):
+                // {(0,1),(2,3)}, {(0,2),(1,3)}, {(0,3),(1,2)}
+                const int blk = 4 * ((grp < 2) ? bA : bB), gi = grp & 1;
+#pragma unroll 1
+                for (int t = 0; t < 3; ++t) {
+                  const int i = (t == 0) ? 2 * gi : gi;
+                  const int j = (t == 0) ? 2 * gi + 1 : (t == 1 ? gi + 2 : 3 - gi);
+                  jpair(blk + i, blk + j);
+                  __syncwarp();
+                }
               }
-              if (li == 0) rot[sweep % 3] = 1;
+#pragma unroll 1
+              for (int t = 0; t < 4; ++t) {
+                jpair(4 * bA + grp, 4 * bB + ((grp + t) & 3));
+                __syncwarp();
+              }
             }
             named_barrier(1, NJ);
           }
