@@ -25,6 +25,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# measured DRAM traffic per unit of work (ncu, see roofline())
+ENV_DRAM_BYTES_PER_SITE_STEP = 6585695744 / (16 * 127 * 128)           # 25.3 KB
+SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE = 64652019200 / (16 * 500 * 128 * 128)   # 493 B
+
 METRIC = "spins proposed/s at L=256 χ=32, BF16/TF32 vs FP64 GPU path; p50/p99 latency"
 UNIT = "spins/s"
 
@@ -405,8 +409,17 @@ def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
     tiles = math.ceil(items / M) * a.R
     samp_bytes = tiles * 2 * L * L * (2 * CHI * CHI) * te + a.R * items * L * L * (2 * CHI) * 4 * 2
     samp_gbs = K * samp_bytes / (samp_union_ms / 1e3) / 1e9
+    # DRAM bytes per unit from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
+    # profile_case 128 32 16 tf32 250, L2-exceeding; profiles/dram_traffic_L128_chi32_R16_tf32.md),
+    # scaled by the units of one launch here; only for the kernels that capture measured
+    env_traffic = samp_traffic = None
+    if a.precision == "tf32" and CHI == 32:
+        env_traffic = ENV_DRAM_BYTES_PER_SITE_STEP * a.R * (L - 1) * L
+        samp_traffic = SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE * a.R * items * L * L
     return dict(kernel="env_build_kernel", bound="alu", achieved=build_tf, peak=alu_peak, unit="TFLOP/s",
-                frac=build_tf / alu_peak, traffic=None,
+                frac=build_tf / alu_peak, traffic=env_traffic,
+                traffic_source=("ncu capture at L=128, 16 realizations, scaled per site step"
+                                if env_traffic is not None else None),
                 peak_source=("derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
                              + (" / 64 (FP64 rate of this part)" if a.precision == "fp64" else "")),
                 algorithmic_flops_per_launch=build_flops, launches=K,
@@ -414,6 +427,7 @@ def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
                 sampler=dict(kernel="sample_tc_kernel" if M == 128 else "sample_kernel", bound="hbm",
                              achieved=samp_gbs, peak=hbm, unit="GB/s", frac=samp_gbs / hbm,
                              algorithmic_bytes_per_launch=samp_bytes, busy_ms=samp_union_ms,
+                             traffic=samp_traffic,
                              peak_source="measured" if "hbm_gbs" in peaks else "fallback"))
 
 
