@@ -50,3 +50,24 @@ def energy(s, Jh, Jv):
 
 def n_bonds(Ly, Lx):
     return Ly * (Lx - 1) + (Ly - 1) * Lx
+
+
+def edge_segment(L):
+    """0-based positions along one edge that the edge magnetisation sums: the paper's 1-based
+    i = L/4 ... 3L/4 inclusive (Sec. III.C, the m_edge equation), i.e. every integer i with
+    L/4 <= i <= 3L/4, shifted by one.  Read literally: L/2 + 1 sites when 4 divides L."""
+    i = np.arange(1, L + 1)
+    return i[(4 * i >= L) & (4 * i <= 3 * L)] - 1
+
+
+def edge_magnetisation(s):
+    """m_edge = (1/(2L)) sum_i (s_{i,1} + s_{1,i} + s_{L,i} + s_{i,L}) over the edge segment,
+    for spins s (..., L, L); the 1/(2L) normalisation is the paper's, read literally
+    (Sec. III.C)."""
+    s = np.asarray(s)
+    L = s.shape[-1]
+    seg = edge_segment(L)
+    tot = (s[..., seg, 0].sum(axis=-1) + s[..., 0, seg].sum(axis=-1) +
+           s[..., L - 1, seg].sum(axis=-1) + s[..., seg, L - 1].sum(axis=-1))
+    return tot / (2.0 * L)
+

@@ -13,13 +13,16 @@ Delta >= 0 or u < exp(Delta), u the Philox uniform of counter
 ``n_therm`` on.
 
 Observables (Sec. III.C): energy E, magnetisation m = (1/N) sum s, the two-replica
-overlap q = (1/N) sum s^(1) s^(2) between chains 0 and 1 at the same step, and the
-Binder ratios U_m = [<m^4>]/[<m^2>]^2 and Q_q = [<q^4>]/[<q^2>]^2 (Eq. eq:binderEA with
-the denominator read as [<q^2>]^2; [<q^2>^2] is also returned).
+overlap q = (1/N) sum s^(1) s^(2) between chains 0 and 1 at the same step, the edge
+magnetisation m_edge (``lattice.edge_magnetisation``), the Binder ratios
+U_m = [<m^4>]/[<m^2>]^2 and Q_q = [<q^4>]/[<q^2>]^2 (Eq. eq:binderEA with the denominator
+read as [<q^2>]^2; [<q^2>^2] is also returned), the overlap susceptibility
+chi_q = (L^2/T) ([<q^2>] - [<q>]^2) (Eq. eq:susEA, with 1/T and the square of the disorder
+mean taken as printed) and the edge susceptibility chi_edge = L [<m_edge^2>].
 """
 import numpy as np
 
-from . import philox
+from . import lattice, philox
 
 
 def metropolis_chain(energy, logq, beta, seed, chain, steps, state=None):
@@ -59,7 +62,7 @@ def chain_observables(spins_cur, energy_cur):
     """
     N = spins_cur.shape[-1] * spins_cur.shape[-2]
     m = spins_cur.reshape(spins_cur.shape[0], spins_cur.shape[1], -1).sum(axis=-1) / N
-    out = dict(E=energy_cur.astype(np.float64), m=m)
+    out = dict(E=energy_cur.astype(np.float64), m=m, m_edge=lattice.edge_magnetisation(spins_cur))
     if spins_cur.shape[0] >= 2:
         a = spins_cur[0].reshape(spins_cur.shape[1], -1)
         b = spins_cur[1].reshape(spins_cur.shape[1], -1)
@@ -71,16 +74,19 @@ def thermal_means(obs, n_therm):
     """Thermal means of one realization over steps >= n_therm (chains pooled for E, m)."""
     E = obs['E'][:, n_therm:]
     m = obs['m'][:, n_therm:]
+    me = obs['m_edge'][:, n_therm:]
     res = dict(E=E.mean(), E2=(E ** 2).mean(), m_abs=np.abs(m).mean(),
-               m2=(m ** 2).mean(), m4=(m ** 4).mean())
+               m2=(m ** 2).mean(), m4=(m ** 4).mean(),
+               m_edge=me.mean(), m_edge_abs=np.abs(me).mean(), m_edge2=(me ** 2).mean())
     if 'q' in obs:
         q = obs['q'][n_therm:]
         res.update(q=q.mean(), q_abs=np.abs(q).mean(), q2=(q ** 2).mean(), q4=(q ** 4).mean())
     return res
 
 
-def disorder_average(per_real):
-    """Disorder means [.] and standard errors over realizations, plus Binder ratios."""
+def disorder_average(per_real, L=None, beta=None):
+    """Disorder means [.] and standard errors over realizations, plus Binder ratios and,
+    given L (and beta for chi_q), the susceptibilities chi_q and chi_edge."""
     keys = per_real[0].keys()
     R = len(per_real)
     out = {}
@@ -91,4 +97,8 @@ def disorder_average(per_real):
     if 'q2' in out:
         out['Q_q'] = out['q4'][0] / out['q2'][0] ** 2
         out['q2_sq'] = float(np.mean([d['q2'] ** 2 for d in per_real]))
+        if L is not None and beta is not None:
+            out['chi_q'] = L * L * beta * (out['q2'][0] - out['q'][0] ** 2)
+    if L is not None and 'm_edge2' in out:
+        out['chi_edge'] = L * out['m_edge2'][0]
     return out
