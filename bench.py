@@ -306,9 +306,9 @@ def main():
         obs += c.observables()
     if world > 1:       # the one cross-rank exchange: per-realization means for [.] averages
         from paper_2409_06538_gb300 import shard
-        dav, _ = shard.gather_disorder_average(obs)
+        dav, _ = shard.gather_disorder_average(obs, L=L, beta=beta)
     else:
-        dav = tn.disorder_average(obs)
+        dav = tn.disorder_average(obs, L, beta)
     spins_per_step = R * a.chains * a.n * L * L
     value = world * spins_per_step * a.steps / elapsed
 
@@ -369,7 +369,7 @@ def main():
                     jacobi_mean_sweeps=mean_sweeps,
                     accepted_proposals_per_s=value / (L * L) * dav["acceptance"],
                     acceptance=dav["acceptance"], clamps=dav["clamps"],
-                    observables={k: dav[k] for k in ("E", "m2", "q2", "U_m", "Q_q")})
+                    observables={k: dav[k] for k in ("E", "m2", "q2", "U_m", "Q_q", "m_edge2", "chi_q", "chi_edge")})
         print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()

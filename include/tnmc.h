@@ -71,7 +71,9 @@ typedef struct {
 
 /* Per-realization thermal means over measured steps (Sec. III.C).  m = (1/N) sum_i s_i,
  * q = (1/N) sum_i s_i^(0) s_i^(1) between the current states of chains 0 and 1 at the same
- * step; E, m statistics pool all chains. */
+ * step; m_edge = (1/2L) sum over the 1-based positions i = L/4 ... 3L/4 (inclusive) of
+ * s_{i,1} + s_{1,i} + s_{L,i} + s_{i,L} (the edge magnetisation of Sec. III.C, normalisation
+ * and segment as printed); E, m and m_edge statistics pool all chains. */
 typedef struct {
   int64_t n_prop;       /* proposals processed by accept (all chains) */
   int64_t n_acc;        /* proposals accepted (excluding each chain's unconditional first) */
@@ -80,6 +82,7 @@ typedef struct {
   int64_t clamps;       /* negative truncated weights clamped to zero while sampling */
   double E, E2, m_abs, m2, m4;
   double q, q_abs, q2, q4;
+  double m_edge, m_edge_abs, m_edge2;
 } tnmc_obs;
 
 typedef struct tnmc_ctx tnmc_ctx;

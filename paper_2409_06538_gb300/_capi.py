@@ -62,7 +62,8 @@ class Obs(ctypes.Structure):
     _fields_ = [("n_prop", c_int64), ("n_acc", c_int64), ("n_meas", c_int64), ("n_meas_q", c_int64),
                 ("clamps", c_int64), ("E", c_double), ("E2", c_double), ("m_abs", c_double),
                 ("m2", c_double), ("m4", c_double), ("q", c_double), ("q_abs", c_double),
-                ("q2", c_double), ("q4", c_double)]
+                ("q2", c_double), ("q4", c_double), ("m_edge", c_double), ("m_edge_abs", c_double),
+                ("m_edge2", c_double)]
 
 
 class ServerOpts(ctypes.Structure):

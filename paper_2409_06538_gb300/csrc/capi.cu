@@ -698,6 +698,7 @@ void obs_from_acc(const double* a, int64_t clamps, tnmc_obs* out) {
   o.E = a[ACC_E] / nm; o.E2 = a[ACC_E2] / nm; o.m_abs = a[ACC_MABS] / nm;
   o.m2 = a[ACC_M2] / nm; o.m4 = a[ACC_M4] / nm;
   o.q = a[ACC_Q] / nq; o.q_abs = a[ACC_QABS] / nq; o.q2 = a[ACC_Q2] / nq; o.q4 = a[ACC_Q4] / nq;
+  o.m_edge = a[ACC_MEDGE] / nm; o.m_edge_abs = a[ACC_MEDGEABS] / nm; o.m_edge2 = a[ACC_MEDGE2] / nm;
 }
 
 // A new batch on a pooled context (used by the request server): n_active <= capacity

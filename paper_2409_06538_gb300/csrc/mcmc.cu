@@ -23,6 +23,33 @@ template <typename T> __device__ __forceinline__ T block_sum(T v, T* red) {
   return out;
 }
 
+// Spins -1 among packed bits b0..b1 (inclusive) of one configuration (bit = site r*L + c).
+__device__ __forceinline__ int neg_in_range(const uint32_t* sp, int b0, int b1) {
+  int neg = 0;
+  for (int w = b0 >> 5; w <= (b1 >> 5); ++w) {
+    uint32_t x = sp[w];
+    const int lo = (w == (b0 >> 5)) ? (b0 & 31) : 0, hi = (w == (b1 >> 5)) ? (b1 & 31) : 31;
+    x >>= lo;
+    const int nb = hi - lo + 1;
+    if (nb < 32) x &= (1u << nb) - 1u;
+    neg += __popc(x);
+  }
+  return neg;
+}
+
+// Edge magnetisation of Sec. III.C: (1/2L) times the sum of the spins on the four edge
+// segments at 1-based positions i = L/4 ... 3L/4 (every integer in that closed interval).
+__device__ __forceinline__ double edge_magnetisation(const uint32_t* sp, int L) {
+  const int i0 = (L + 3) / 4 - 1, i1 = (3 * L) / 4 - 1;
+  int neg = neg_in_range(sp, i0, i1) + neg_in_range(sp, (L - 1) * L + i0, (L - 1) * L + i1);
+  for (int r = i0; r <= i1; ++r) {
+    const int a = r * L, b = r * L + L - 1;
+    neg += (int)((sp[a >> 5] >> (a & 31)) & 1u) + (int)((sp[b >> 5] >> (b & 31)) & 1u);
+  }
+  const int nseg = i1 - i0 + 1;
+  return (double)(4 * nseg - 2 * neg) / (2.0 * L);
+}
+
 // One CTA per realization.  Phase 1: each chain's decisions in step order (one thread per
 // chain).  Phase 2: observables of the current states after every step.  Phase 3: carry the
 // final current state to the next call.
@@ -79,7 +106,7 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
 
   // ---- phase 2: observables
   const double invN = 1.0 / (double)N;
-  double sE = 0, sE2 = 0, sMa = 0, sM2 = 0, sM4 = 0, nm = 0;
+  double sE = 0, sE2 = 0, sMa = 0, sM2 = 0, sM4 = 0, nm = 0, sEd = 0, sEda = 0, sEd2 = 0;
   // items are dealt to threads by (chain, step < lim), so the sums depend only on the
   // realization's own proposals, whatever the call's n
   for (int idx = tid; idx < nc * lim; idx += blockDim.x) {
@@ -92,6 +119,9 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
     const double m = (c >= 0 ? (double)a.magnet[sidx * n + c] : (double)a.cur_magnet[sidx]) * invN;
     const double m2 = m * m;
     sE += E; sE2 += E * E; sMa += fabs(m); sM2 += m2; sM4 += m2 * m2; nm += 1.0;
+    const uint32_t* sp = c >= 0 ? a.spins_packed + (sidx * n + c) * a.words : a.cur_spins + sidx * a.words;
+    const double me = edge_magnetisation(sp, a.L);
+    sEd += me; sEda += fabs(me); sEd2 += me * me;
   }
   double sq = 0, sqa = 0, sq2 = 0, sq4 = 0, nq = 0;
   if (nc >= 2) {
@@ -114,6 +144,7 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
   sM2 = block_sum(sM2, red); sM4 = block_sum(sM4, red); nm = block_sum(nm, red);
   sq = block_sum(sq, red); sqa = block_sum(sqa, red); sq2 = block_sum(sq2, red);
   sq4 = block_sum(sq4, red); nq = block_sum(nq, red);
+  sEd = block_sum(sEd, red); sEda = block_sum(sEda, red); sEd2 = block_sum(sEd2, red);
   if (tid == 0) {
     double* acc = a.acc + (size_t)real * ACC_SLOTS;
     double na = 0;
@@ -124,6 +155,7 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
     acc[ACC_NMEASQ] += nq;
     acc[ACC_E] += sE; acc[ACC_E2] += sE2; acc[ACC_MABS] += sMa; acc[ACC_M2] += sM2; acc[ACC_M4] += sM4;
     acc[ACC_Q] += sq; acc[ACC_QABS] += sqa; acc[ACC_Q2] += sq2; acc[ACC_Q4] += sq4;
+    acc[ACC_MEDGE] += sEd; acc[ACC_MEDGEABS] += sEda; acc[ACC_MEDGE2] += sEd2;
   }
   __syncthreads();
 

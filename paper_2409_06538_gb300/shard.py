@@ -16,12 +16,13 @@ def shard_seeds(seeds, rank, world):
     return seeds[start:start + base + (1 if rank < extra else 0)]
 
 
-def gather_disorder_average(per_realization, group=None):
+def gather_disorder_average(per_realization, group=None, L=None, beta=None):
     """All-gather the per-realization observable dicts of every rank (torch.distributed,
-    any backend) and return the disorder average over all realizations on every rank."""
+    any backend) and return the disorder average over all realizations on every rank
+    (with the susceptibilities when L and beta are given)."""
     import torch.distributed as dist
     world = dist.get_world_size(group)
     parts = [None] * world
     dist.all_gather_object(parts, list(per_realization), group=group)
     merged = [o for part in parts for o in part]
-    return disorder_average(merged), len(merged)
+    return disorder_average(merged, L, beta), len(merged)

@@ -182,10 +182,13 @@ class TNMC:
             pass
 
 
-def disorder_average(obs):
+def disorder_average(obs, L=None, beta=None):
     """Disorder means [.] and standard errors over per-realization thermal means, with the
-    Binder ratios U_m = [<m^4>]/[<m^2>]^2 and Q_q = [<q^4>]/[<q^2>]^2 (Sec. III.C)."""
-    keys = ["E", "E2", "m_abs", "m2", "m4", "q", "q_abs", "q2", "q4"]
+    Binder ratios U_m = [<m^4>]/[<m^2>]^2 and Q_q = [<q^4>]/[<q^2>]^2, and given L (and beta)
+    the susceptibilities chi_q = (L^2/T)([<q^2>] - [<q>]^2) and chi_edge = L [<m_edge^2>]
+    (Sec. III.C, Eq. eq:susEA)."""
+    keys = ["E", "E2", "m_abs", "m2", "m4", "q", "q_abs", "q2", "q4", "m_edge", "m_edge_abs", "m_edge2"]
+    keys = [k for k in keys if k in obs[0]]
     R = len(obs)
     out = {}
     for k in keys:
@@ -197,4 +200,8 @@ def disorder_average(obs):
     nprop = sum(o["n_prop"] for o in obs)
     out["acceptance"] = nacc / max(1, nprop)
     out["clamps"] = int(sum(o["clamps"] for o in obs))
+    if L is not None and beta is not None:
+        out["chi_q"] = L * L * beta * (out["q2"][0] - out["q"][0] ** 2)
+    if L is not None and "m_edge2" in out:
+        out["chi_edge"] = L * out["m_edge2"][0]
     return out

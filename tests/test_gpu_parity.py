@@ -184,7 +184,7 @@ def test_metropolis_and_observables_parity(tn):
             cur_E.append(E[k, ch][cur])
         o = metropolis.chain_observables(np.stack(cur_sp), np.stack(cur_E))
         ref = metropolis.thermal_means(o, n_therm)
-        for key in ("E", "E2", "m_abs", "m2", "m4", "q", "q_abs", "q2", "q4"):
+        for key in ("E", "E2", "m_abs", "m2", "m4", "q", "q_abs", "q2", "q4", "m_edge", "m_edge_abs", "m_edge2"):
             assert abs(obs[k][key] - ref[key]) <= 1e-12 * max(1.0, abs(ref[key])), key
         assert obs[k]["n_prop"] == 2 * 2 * n
         assert obs[k]["n_acc"] == int(fl[k].sum()) - 2
@@ -216,7 +216,7 @@ def test_observables_match_independent_oracle_run(tn):
             cs.append(pr["spins"][cur]); ce.append(pr["energy"][cur])
         per.append(metropolis.thermal_means(metropolis.chain_observables(np.stack(cs), np.stack(ce)), n_therm))
     o = metropolis.disorder_average(per)
-    for key in ("E", "m2", "q2"):
+    for key in ("E", "m2", "q2", "m_edge2"):
         se = np.hypot(g[key][1], o[key][1])
         assert abs(g[key][0] - o[key][0]) <= 2 * se + 1e-12, key
     assert abs(g["U_m"] - o["U_m"]) < 0.05

@@ -22,7 +22,7 @@ int main(void) {
   printf("tnmc_server_opts %zu\n", sizeof(tnmc_server_opts));
   printf("tnmc_request %zu\n", sizeof(tnmc_request));
   printf("tnmc_result %zu\n", sizeof(tnmc_result));
-  F(tnmc_opts, stream); F(tnmc_obs, E); F(tnmc_obs, q4);
+  F(tnmc_opts, stream); F(tnmc_obs, E); F(tnmc_obs, q4); F(tnmc_obs, m_edge2);
   F(tnmc_server_opts, linger_us); F(tnmc_server_opts, device); F(tnmc_server_opts, mem_budget);
   F(tnmc_request, L); F(tnmc_request, chi); F(tnmc_request, p); F(tnmc_request, beta); F(tnmc_request, n_samples);
   F(tnmc_result, status); F(tnmc_result, batch_size); F(tnmc_result, log_z); F(tnmc_result, obs);
