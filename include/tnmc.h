@@ -167,7 +167,10 @@ tnmc_status tnmc_eval_conditionals(tnmc_ctx* ctx, int n, const int8_t* spins_dev
  *   n_accepted_host: total accepted in this call (nullable; passing it synchronises). */
 tnmc_status tnmc_accept(tnmc_ctx* ctx, uint8_t* accepted_dev, int64_t* n_accepted_host);
 
-/* Per-realization thermal means (host array of n_real tnmc_obs).  Synchronises. */
+/* Per-realization thermal means (host array of n_real tnmc_obs).  Synchronises.  Every
+ * realization is filled in before the context's status is returned: on TNMC_ERR_NUMERIC the
+ * realizations that tnmc_realization_status flags carry meaningless values and the others are
+ * valid; on other errors nothing is meaningful. */
 tnmc_status tnmc_observables(tnmc_ctx* ctx, tnmc_obs* out_host);
 
 /* Reset chain states and observable accumulators (the environments stay cached). */

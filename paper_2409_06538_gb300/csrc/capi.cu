@@ -528,15 +528,16 @@ tnmc_status tnmc_accept(tnmc_ctx* c, uint8_t* accepted_dev, int64_t* n_accepted_
 
 tnmc_status tnmc_observables(tnmc_ctx* c, tnmc_obs* out_host) {
   if (!c || !out_host) return fail(c, TNMC_ERR_ARG, "NULL argument");
-  tnmc_status s = check_status(c);
-  if (s) return s;
+  cudaError_t es = cudaStreamSynchronize(c->stream);
+  if (es != cudaSuccess) return cuda_fail(c, es, "synchronise");
   std::vector<double> acc((size_t)c->n_real * tnmc::ACC_SLOTS);
   std::vector<int64_t> cl(c->n_real);
   cudaError_t e = cudaMemcpy(acc.data(), c->acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(cl.data(), c->clamps, cl.size() * sizeof(int64_t), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "observables copy");
   for (int k = 0; k < c->n_real; ++k) tnmc::obs_from_acc(&acc[(size_t)k * tnmc::ACC_SLOTS], cl[k], &out_host[k]);
-  return TNMC_OK;
+  // every realization is filled in; a numeric failure of some is reported after the fact
+  return check_status(c);
 }
 
 tnmc_status tnmc_reset_chains(tnmc_ctx* c) {

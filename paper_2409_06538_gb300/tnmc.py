@@ -131,9 +131,13 @@ class TNMC:
         self._chk(self.lib.tnmc_accept(self.ctx, _ptr(acc), _c.byref(cnt) if count else None))
         return dict(flags=acc, count=cnt.value if count else None)
 
-    def observables(self):
+    def observables(self, allow_numeric=False):
+        """Per-realization thermal means.  With allow_numeric, a numeric failure of some
+        realizations does not raise: check realization_status() to drop them."""
         arr = (_capi.Obs * self.n_real)()
-        self._chk(self.lib.tnmc_observables(self.ctx, arr))
+        code = self.lib.tnmc_observables(self.ctx, arr)
+        if not (allow_numeric and code == 4):
+            self._chk(code)
         return [{k: getattr(o, k) for k, _ in _capi.Obs._fields_} for o in arr]
 
     def reset_chains(self):
