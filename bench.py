@@ -26,8 +26,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 # measured DRAM traffic per unit of work (ncu, see roofline())
-ENV_DRAM_BYTES_PER_SITE_STEP = 6585695744 / (16 * 127 * 128)           # 25.3 KB
-SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE = 64652019200 / (16 * 500 * 128 * 128)   # 493 B
+ENV_DRAM_BYTES_PER_SITE_STEP = 6372628736 / (16 * 127 * 128)           # 24.5 KB
+SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE = 64751584768 / (16 * 500 * 128 * 128)   # 494 B
 
 METRIC = "spins proposed/s at L=256 χ=32, BF16/TF32 vs FP64 GPU path; p50/p99 latency"
 UNIT = "spins/s"
@@ -36,7 +36,8 @@ UNIT = "spins/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed batches (default: as many as run at once, at least 4)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32", choices=["bf16", "tf32", "fp32", "fp64"])
@@ -46,7 +47,8 @@ def parse():
     ap.add_argument("--n", type=int, default=250, help="proposals per chain per step")
     ap.add_argument("--chains", type=int, default=2)
     ap.add_argument("--p", type=float, default=0.109)
-    ap.add_argument("--inflight", type=int, default=4, help="batches in flight (contexts on streams)")
+    ap.add_argument("--inflight", type=int, default=0,
+                    help="batches in flight (contexts on streams); 0 = as many as the SMs hold at once")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
@@ -117,6 +119,8 @@ def oracle_rate(L, chi, p, n_props_per_real, cores, budget_s):
 
 
 def run_reference(a, rank, world):
+    if a.steps is None:
+        a.steps = 4
     if rank != 0:
         return
     cores = os.cpu_count() or 1
@@ -226,6 +230,12 @@ def main():
     dev = torch.device("cuda", local)
     beta = tn.nishimori_beta(a.p)
     R, L = a.R, a.L
+    per_sm, n_sms = tn.env_build_occupancy(L, a.chi, a.precision)
+    slots = per_sm * n_sms                         # environment-build CTAs the GPU holds at once
+    if a.inflight <= 0:
+        a.inflight = max(1, slots // R)
+    if a.steps is None:
+        a.steps = max(4, a.inflight)
     S = max(1, min(a.inflight, a.steps))          # batches in flight (one context + stream each)
 
     def seeds_for(step):
@@ -356,6 +366,7 @@ def main():
     if rank == 0:
         cfg = _config(a)
         cfg["inflight_batches"] = S
+        cfg["env_build_ctas_per_sm"] = per_sm
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=a.steps, warmup=a.warmup,
                     ms_per_step=1e3 * elapsed / a.steps, higher_is_better=True, scaling="weak",
                     vs_baseline=None, dtype=a.precision,

@@ -237,6 +237,15 @@ tnmc_status tnmc_realization_status(tnmc_ctx* ctx, int32_t* out_host);
 /* Kernel launch accounting: number of kernels this context launched since creation. */
 int64_t tnmc_launch_count(const tnmc_ctx* ctx);
 
+/* Concurrency of the environment build on the current device: *ctas_per_sm gets how many
+ * realizations (one CTA each) one SM holds at once for this L, chi and precision (shared
+ * memory and registers decide), *num_sms (nullable) the SM count.  A batch of R
+ * realizations fills R of ctas_per_sm * num_sms slots; callers size the number of batches
+ * they keep in flight from it.  TNMC_ERR_ARG / TNMC_ERR_UNSUPPORTED for bad arguments,
+ * TNMC_ERR_CUDA without a device. */
+tnmc_status tnmc_env_build_occupancy(int L, int chi, int precision, int32_t* ctas_per_sm,
+                                     int32_t* num_sms);
+
 /* Device memory accounting.  tnmc_device_bytes: bytes the context holds now (its buffers
  * grow once to the largest n passed to tnmc_propose).  tnmc_estimate_device_bytes: bytes a
  * context of these arguments would hold after proposals of up to n_max per chain, without

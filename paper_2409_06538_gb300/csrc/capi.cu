@@ -598,6 +598,21 @@ tnmc_status tnmc_realization_status(tnmc_ctx* c, int32_t* out_host) {
   return TNMC_OK;
 }
 
+tnmc_status tnmc_env_build_occupancy(int L, int chi, int precision, int32_t* ctas_per_sm, int32_t* num_sms) {
+  if (!ctas_per_sm || L < 2 || L > 4096 || precision < 0 || precision > 3)
+    return fail(nullptr, TNMC_ERR_ARG, "bad arguments");
+  const int CHI = round_chi(chi);
+  if (chi < 1 || CHI == 0) return fail(nullptr, TNMC_ERR_UNSUPPORTED, "chi outside 1..32");
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaError_t e = tnmc::env_build_occupancy(L, CHI, precision, &per_sm);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "occupancy query");
+  *ctas_per_sm = per_sm;
+  if (num_sms) *num_sms = sms;
+  return TNMC_OK;
+}
+
 size_t tnmc_device_bytes(const tnmc_ctx* c) {
   if (!c) return 0;
   size_t b = 0;

@@ -133,10 +133,12 @@ template <typename T, int CHI> struct JStride {
 
 template <typename T, int CHI>
 __host__ __device__ constexpr size_t env_smem_elems() {
-  // backward: M, R (D*D each), Y, V (D*DP each) + P (D*CHI) + Q (2*CHI*CHI) + tile (2*CHI*CHI)
-  // forward : X (2D*D, aliases M and Y) + R (D*D) + tile
+  // backward: M, R (D*D each), Y, V (D*DP each) + tile (2*CHI*CHI); P (D*CHI) lives in the Y
+  //           region and Q (2*CHI*CHI) in the V region between their uses
+  // forward : X (2D*D, aliases M and Y) + R (D*D) + tile; the Householder vectors use V
+  // (FP32, CHI = 32: 72 KB, so three CTAs fit on one SM)
   return (size_t)2 * (2 * CHI) * (2 * CHI) + (size_t)2 * (2 * CHI) * JStride<T, CHI>::DP +
-         (size_t)(2 * CHI) * CHI + 2 * (size_t)2 * CHI * CHI;
+         (size_t)2 * CHI * CHI;
 }
 
 template <int CHI> struct Pair {
@@ -149,7 +151,7 @@ template <int CHI> struct Pair {
 };
 
 template <typename T, typename TE, int CHI>
-__global__ void __launch_bounds__(EnvCfg<CHI>::NT, 2)
+__global__ void __launch_bounds__(EnvCfg<CHI>::NT, sizeof(T) == 8 ? 1 : 3)
 env_build_kernel(EnvBuildArgs<T, TE> args) {
   using C = EnvCfg<CHI>;
   constexpr int D = C::D, NWARP = C::NWARP, NT = C::NT, TILE = C::TILE;
@@ -167,9 +169,12 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
   T* Yc = Mc + D * D;         // n columns of stride DP (rows >= D zero)
   T* Vc = Yc + D * DP;        // n columns of stride DP (rows >= n zero)
   T* Rc = Vc + D * DP;        // D x D   col-major R_c
-  T* Ps = Rc + D * D;         // D x CHI col-major: P[(b,be)][g] at g*D + b*CHI + be
-  T* Qs = Ps + D * CHI;       // 2 x CHI x CHI: Q[b][al][g]
-  T* Bt = Qs + TILE;          // previous-row tile [y][al][be]
+  T* Bt = Rc + D * D;         // previous-row tile [y][al][be]
+  // P is written after the SVD (Y is dead by then) and read by the next site's Q = B P before
+  // that site's Y is formed; Q is written after this site's V is dead and read before the next
+  // V is initialised: so P takes the Y region and Q the V region
+  T* Ps = Yc;                 // D x CHI col-major: P[(b,be)][g] at g*D + b*CHI + be
+  T* Qs = Vc;                 // 2 x CHI x CHI: Q[b][al][g]
   // forward-phase layout (aliases M/Y/V; R stays at Rc)
   T* Xs = sm;                 // 2D x D col-major
 
@@ -177,7 +182,9 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
   int8_t* jv_s = reinterpret_cast<int8_t*>(Bt + TILE);        // Jv[r][c], L entries
   int8_t* jh_s = jv_s + args.L;                                // Jh[r+1][c], L-1 entries
   const T eb = (T)exp(beta), ebm = (T)exp(-beta);             // exp(+-beta): every Boltzmann weight
-  __shared__ T vbuf[2][2 * D];      // Householder vectors (double-buffered)
+  T (*vbuf)[2 * D] = reinterpret_cast<T (*)[2 * D]>(Vc);   // Householder vectors (double-
+                                                            // buffered; the V region is idle
+                                                            // in the forward sweep)
   __shared__ T vcoef[2];
   __shared__ T red[32];
   __shared__ T sig[D];
@@ -747,6 +754,31 @@ cudaError_t launch_env_build(const EnvBuildArgs<T, TE>& a, int CHI, cudaStream_t
 template cudaError_t launch_env_build<double, double>(const EnvBuildArgs<double, double>&, int, cudaStream_t);
 template cudaError_t launch_env_build<float, float>(const EnvBuildArgs<float, float>&, int, cudaStream_t);
 template cudaError_t launch_env_build<float, __nv_bfloat16>(const EnvBuildArgs<float, __nv_bfloat16>&, int, cudaStream_t);
+
+template <typename T, typename TE, int CHI>
+static cudaError_t occupancy_t(int L, int* per_sm) {
+  using C = EnvCfg<CHI>;
+  const size_t smem = env_smem_elems<T, CHI>() * sizeof(T) + (size_t)2 * L + 16;
+  cudaError_t e = cudaFuncSetAttribute(env_build_kernel<T, TE, CHI>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, env_build_kernel<T, TE, CHI>, C::NT, smem);
+}
+
+cudaError_t env_build_occupancy(int L, int CHI, int precision, int* per_sm) {
+#define TNMC_OCC(T, TE)                                           \
+  switch (CHI) {                                                  \
+    case 4: return occupancy_t<T, TE, 4>(L, per_sm);              \
+    case 8: return occupancy_t<T, TE, 8>(L, per_sm);              \
+    case 16: return occupancy_t<T, TE, 16>(L, per_sm);            \
+    case 32: return occupancy_t<T, TE, 32>(L, per_sm);            \
+    default: return cudaErrorInvalidValue;                        \
+  }
+  if (precision == 0) { TNMC_OCC(double, double) }
+  if (precision == 2) { TNMC_OCC(float, __nv_bfloat16) }
+  TNMC_OCC(float, float)
+#undef TNMC_OCC
+}
 
 size_t env_build_smem_bytes(int CHI, bool fp64) {
   const size_t el = fp64 ? 8 : 4;

@@ -33,6 +33,8 @@ struct EnvBuildArgs {
 template <typename T, typename TE>
 cudaError_t launch_env_build(const EnvBuildArgs<T, TE>& a, int CHI, cudaStream_t st);
 size_t env_build_smem_bytes(int CHI, bool fp64);
+// Environment-build CTAs (one per realization) that fit on one SM at this L, CHI and precision.
+cudaError_t env_build_occupancy(int L, int CHI, int precision, int* per_sm);
 
 struct SampleArgs {
   int L, n_real, n_chains, n;      // proposals per chain in this call

@@ -26,6 +26,15 @@ def nishimori_beta(p):
     return 0.5 * math.log((1.0 - p) / p)
 
 
+def env_build_occupancy(L, chi, precision="tf32"):
+    """(realizations per SM, SM count) for the environment build on the current device."""
+    lib = _capi.load()
+    per, sms = _c.c_int32(0), _c.c_int32(0)
+    _capi.check(lib.tnmc_env_build_occupancy(int(L), int(chi), _capi.PRECISIONS[precision], _c.byref(per),
+                                             _c.byref(sms)))
+    return per.value, sms.value
+
+
 def couplings_pmj(L, seeds, p, stream=None):
     """Seeded +-J couplings of len(seeds) realizations on the device: int8 [R, 2L(L-1)]."""
     lib = _capi.load()
