@@ -126,3 +126,4 @@ def test_invalid_request_is_refused(tn):
             srv.submit(1, 8, 4, 1.5, 1.0, 10)        # p outside [0, 1]
         with pytest.raises(tn._capi.TnmcError):
             srv.wait(12345, timeout=0.1)             # unknown id
+
