@@ -237,6 +237,15 @@ tnmc_status tnmc_realization_status(tnmc_ctx* ctx, int32_t* out_host);
 /* Kernel launch accounting: number of kernels this context launched since creation. */
 int64_t tnmc_launch_count(const tnmc_ctx* ctx);
 
+/* Failure-detection self-test (the paper has no counterpart).  Runs, on the current device and
+ * the default stream, the bounded mbarrier wait that guards the tensor-core sampler's MMA
+ * completions, in a one-CTA probe kernel: with arrive = 0 nothing arrives on the barrier, so
+ * the wait gives up after 4096 polls, the kernel records the timeout in a status word and
+ * returns normally, and this call returns TNMC_ERR_TIMEOUT; with arrive != 0 one thread
+ * arrives first and the call returns TNMC_OK.  *elapsed_us (nullable) gets the probe's device
+ * time.  The CUDA context stays usable afterwards.  Synchronises. */
+tnmc_status tnmc_selftest_bounded_wait(int arrive, int64_t* elapsed_us);
+
 /* Concurrency of the environment build on the current device: *ctas_per_sm gets how many
  * realizations (one CTA each) one SM holds at once for this L, chi and precision (shared
  * memory and registers decide), *num_sms (nullable) the SM count.  A batch of R

@@ -40,6 +40,7 @@ SIGNATURES = {
     "tnmc_build_env_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                                        c_void_p, c_void_p, c_void_p]),
     "tnmc_device_bytes": (c_size_t, [c_void_p]),
+    "tnmc_selftest_bounded_wait": (c_int, [c_int, c_int64_p]),
     "tnmc_env_build_occupancy": (c_int, [c_int, c_int, c_int, c_int32_p, c_int32_p]),
     "tnmc_realization_status": (c_int, [c_void_p, c_int32_p]),
     "tnmc_estimate_device_bytes": (c_size_t, [c_int, c_int, c_int, c_void_p, c_int]),

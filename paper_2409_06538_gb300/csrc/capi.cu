@@ -598,6 +598,30 @@ tnmc_status tnmc_realization_status(tnmc_ctx* c, int32_t* out_host) {
   return TNMC_OK;
 }
 
+tnmc_status tnmc_selftest_bounded_wait(int arrive, int64_t* elapsed_us) {
+  unsigned* st = nullptr;
+  cudaError_t e = cudaMalloc(&st, sizeof(unsigned));
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, TNMC_ERR_OOM, "status word"); }
+  unsigned h = 0;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  e = cudaMemset(st, 0, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e == cudaSuccess) e = cudaEventRecord(t0, nullptr);
+  if (e == cudaSuccess) e = tnmc::launch_wait_probe(arrive, 1ll << 12, st, nullptr);
+  if (e == cudaSuccess) e = cudaEventRecord(t1, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&h, st, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  cudaFree(st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "wait self-test");
+  if (elapsed_us) *elapsed_us = (int64_t)(1000.0f * ms);
+  if (h & tnmc::ST_TIMEOUT) return fail(nullptr, TNMC_ERR_TIMEOUT, "the bounded wait ran out (as the self-test intends when nothing arrives)");
+  return TNMC_OK;
+}
+
 tnmc_status tnmc_env_build_occupancy(int L, int chi, int precision, int32_t* ctas_per_sm, int32_t* num_sms) {
   if (!ctas_per_sm || L < 2 || L > 4096 || precision < 0 || precision > 3)
     return fail(nullptr, TNMC_ERR_ARG, "bad arguments");

@@ -63,6 +63,8 @@ struct SampleArgs {
 cudaError_t launch_sample(const SampleArgs& a, int precision, int CHI, int num_sms, cudaStream_t st);
 // tensor-core (tcgen05, 3xTF32) sampler of the mixed path; CHI 16 or 32
 bool sample_tc_supported(int CHI);
+// Self-test of the sampler's bounded mbarrier wait (see sample_tc.cu).
+cudaError_t launch_wait_probe(int arrive, long long limit, unsigned* status_dev, cudaStream_t st);
 cudaError_t launch_sample_tc(const SampleArgs& a, int CHI, int num_sms, cudaStream_t st);
 size_t sample_tc_work_bytes(int L, int CHI, int num_sms);
 size_t sample_work_bytes(int L, int CHI, int precision, int num_sms);

@@ -51,9 +51,9 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(mbar)));
 }
 // Bounded wait for the given phase parity; false when the limit ran out.
-__device__ __forceinline__ bool wait_parity(uint64_t* mbar, uint32_t parity) {
+__device__ __forceinline__ bool wait_parity(uint64_t* mbar, uint32_t parity, long long limit = 1ll << 20) {
   uint32_t done = 0;
-  for (long long it = 0; it < (1ll << 20) && !done; ++it) {
+  for (long long it = 0; it < limit && !done; ++it) {
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(done) : "r"(su32(mbar)), "r"(parity) : "memory");
   }
@@ -478,6 +478,29 @@ static cudaError_t launch_tc_t(const SampleArgs& a, int num_sms, cudaStream_t st
 }
 
 bool sample_tc_supported(int CHI) { return CHI == 16 || CHI == 32; }
+
+// Self-test of the bounded wait the sampler uses on its MMA completions: one CTA waits on an
+// mbarrier of arrival count 1; with arrive != 0 one thread arrives first, otherwise nothing
+// does and every wait must give up after `limit` polls and record ST_TIMEOUT.  The kernel
+// returns normally either way.
+__global__ void wait_probe_kernel(int arrive, long long limit, unsigned* status) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tc::su32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(tc::su32(&mbar)) : "memory");
+  }
+  __syncthreads();
+  if (!tc::wait_parity(&mbar, 0u, limit)) set_status(status, ST_TIMEOUT);
+}
+
+cudaError_t launch_wait_probe(int arrive, long long limit, unsigned* status_dev, cudaStream_t st) {
+  wait_probe_kernel<<<1, 32, 0, st>>>(arrive, limit, status_dev);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sample_tc(const SampleArgs& a, int CHI, int num_sms, cudaStream_t st) {
   if (CHI == 32) return launch_tc_t<32>(a, num_sms, st);

@@ -24,3 +24,24 @@ def test_chi_autotuning_prefers_the_cheapest_accepted_proposal(tn):
         assert r["failed_realizations"] > 0 or 0.0 <= r["p_a"] <= 1.0
     costs = {r["chi"]: r["s_per_accepted"] for r in table}
     assert costs[best] == min(costs.values())
+
+
+def test_bounded_wait_times_out_and_the_context_survives(tn):
+    """Failure detection without a fault: the sampler's bounded mbarrier wait, run on a barrier
+    that nothing arrives on, gives up, the kernel records TNMC_ERR_TIMEOUT and returns; with one
+    arrival it succeeds; afterwards the same CUDA context still runs a full build."""
+    import ctypes
+    import numpy as np
+    from paper_2409_06538_gb300 import _capi
+    lib = _capi.load()
+    us = ctypes.c_int64(-1)
+    assert lib.tnmc_selftest_bounded_wait(1, ctypes.byref(us)) == 0
+    assert lib.tnmc_selftest_bounded_wait(0, ctypes.byref(us)) == 5      # TNMC_ERR_TIMEOUT
+    assert 0 <= us.value < 1_000_000                                     # gave up within a second
+    J = tn.couplings_pmj(6, [1, 2], 0.1)
+    t = tn.TNMC(6, J, 1.0, [1, 2], 4, precision="fp64")
+    assert np.isfinite(t.build_env()).all()
+    t.propose(8, 0, outputs=False)
+    t.accept()
+    assert all(o["n_prop"] == 16 for o in t.observables())
+    t.close()
