@@ -8,7 +8,9 @@ Default workload (one GPU): L = 256, chi = 32, p = 0.109 on the Nishimori line,
 64 realizations x 2 chains x 250 proposals (500 proposals per realization) per step, mixed
 precision (FP32 environment build and cache, 3xTF32 tensor-core sampling, FP64 log-norms,
 log q and Metropolis).  Up to --inflight steps run concurrently, one context and CUDA
-stream each (continuous batching: a batch's environment build leaves most SMs free).
+stream each (continuous batching: a batch's environment build leaves most SMs free); by default
+as many batches as the SMs hold environment-build CTAs (seven here, 448 of 456 slots), and as
+many timed steps.
 Under torchrun every rank runs its own batches (weak scaling, no data-path collective).
 Prints one JSON line on rank 0.
 """

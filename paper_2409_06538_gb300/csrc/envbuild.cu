@@ -116,8 +116,8 @@ __device__ __forceinline__ void prefetch_async(void* smem, const void* gmem, int
 
 template <int CHI> struct EnvCfg {
   static constexpr int D = 2 * CHI;                 // MPO bond x MPS bond
-  // 8 lanes per Jacobi pair (8*CHI threads); CHI = 32 runs 256 threads so that two
-  // realizations fit on one SM (registers and shared memory)
+  // 8 lanes per Jacobi pair (8*CHI threads); CHI = 32 runs 256 threads so that three
+  // realizations fit on one SM in FP32 (80 registers, 72 KB of shared memory each)
   static constexpr int NWARP = CHI < 4 ? 4 : (CHI > 8 ? 8 : CHI);
   static constexpr int NT = 32 * NWARP;
   static constexpr int TILE = 2 * CHI * CHI;        // [y][alpha][beta]
