@@ -104,7 +104,7 @@ tnmc_status tnmc_couplings_pmj(int L, int n_real, const uint64_t* seeds_host, do
  *   beta_host : n_real inverse temperatures (Eq. P); on the Nishimori line
  *               beta = 0.5 ln((1-p)/p) (Sec. III.A);
  *   seeds_host: n_real Philox keys for the spin and accept draws;
- *   chi       : 1 <= chi <= 32.
+ *   chi       : 1 <= chi <= 64 (<= 32 on the FP64 path; TNMC_ERR_UNSUPPORTED above).
  * Allocates the environment cache (n_real * L * L * 2 chi^2 words) and all scratch on the
  * current CUDA device.  Errors: TNMC_ERR_ARG, TNMC_ERR_OOM, TNMC_ERR_UNSUPPORTED, TNMC_ERR_CUDA. */
 tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double* beta_host,
@@ -298,7 +298,7 @@ typedef struct {
 typedef struct {
   uint64_t seed;     /* realization seed: couplings and every draw (as in tnmc_couplings_pmj) */
   int L;             /* lattice side, 2..4096 */
-  int chi;           /* MPS bond dimension, 1..32 */
+  int chi;           /* MPS bond dimension, 1..64 (1..32 when the server runs FP64) */
   double p;          /* probability of an antiferromagnetic bond, [0, 1] */
   double beta;       /* inverse temperature, finite and > 0 */
   int n_samples;     /* proposals per chain, >= 1 */

@@ -39,6 +39,7 @@ struct tnmc_ctx {
   double* logz = nullptr;
   void* rowbuf = nullptr;
   void* Rstore = nullptr;
+  void* mscratch = nullptr;       // environment-build M matrices for chi = 64 (nullptr otherwise)
   long long* stats = nullptr;
   unsigned* status = nullptr;
   unsigned* rstatus = nullptr;    // per-realization status bits (numeric failures of its proposals)
@@ -123,6 +124,7 @@ int round_chi(int chi) {
   if (chi <= 8) return 8;
   if (chi <= 16) return 16;
   if (chi <= 32) return 32;
+  if (chi <= 64) return 64;
   return 0;
 }
 
@@ -147,11 +149,12 @@ tnmc_status check_status(tnmc_ctx* c) {
 // Device bytes of every buffer a context holds, one function for the allocation and the
 // capacity estimate so that the two cannot drift apart.
 struct CtxSizes {
-  size_t J, beta, seeds, pvec, nlimit, env, kdim, dqr, lam, logz, rowbuf, Rstore, stats, status, rstatus,
+  size_t J, beta, seeds, pvec, nlimit, env, kdim, dqr, lam, logz, rowbuf, Rstore, mscratch, stats, status, rstatus,
       work, work_tc, clamps, have_state, cur_logq, cur_energy, cur_magnet, cur_spins, acc;
   size_t total() const {
-    return J + beta + seeds + pvec + nlimit + env + kdim + dqr + lam + logz + rowbuf + Rstore + stats + status +
-           rstatus + work + work_tc + clamps + have_state + cur_logq + cur_energy + cur_magnet + cur_spins + acc;
+    return J + beta + seeds + pvec + nlimit + env + kdim + dqr + lam + logz + rowbuf + Rstore + mscratch + stats +
+           status + rstatus + work + work_tc + clamps + have_state + cur_logq + cur_energy + cur_magnet + cur_spins +
+           acc;
   }
 };
 
@@ -170,6 +173,7 @@ CtxSizes ctx_sizes(int L, int n_real, int CHI, int precision, int n_chains, int 
   z.logz = 8 * R;
   z.rowbuf = R * 2 * L * tile * tsz;
   z.Rstore = R * L * D * D * tsz;
+  z.mscratch = CHI > 32 ? R * D * D * tsz : 0;     // M of the environment build when it leaves shared memory
   z.stats = 4 * sizeof(long long) * R;
   z.status = sizeof(unsigned);
   z.rstatus = sizeof(unsigned) * R;
@@ -237,7 +241,9 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
   if (n_real < 1) return fail(nullptr, TNMC_ERR_ARG, "n_real must be >= 1");
   if (!couplings || !beta_host || !seeds_host || !opts) return fail(nullptr, TNMC_ERR_ARG, "NULL input");
   if (chi < 1) return fail(nullptr, TNMC_ERR_ARG, "chi must be >= 1");
-  if (round_chi(chi) == 0) return fail(nullptr, TNMC_ERR_UNSUPPORTED, "chi > 32 is not built into this library");
+  if (round_chi(chi) == 0) return fail(nullptr, TNMC_ERR_UNSUPPORTED, "chi > 64 is not built into this library");
+  if (chi > 32 && opts && opts->precision == TNMC_FP64)
+    return fail(nullptr, TNMC_ERR_UNSUPPORTED, "the FP64 path is built for chi <= 32 (chi = 64 needs 256 KB of shared memory)");
   if (opts->precision < 0 || opts->precision > 3) return fail(nullptr, TNMC_ERR_ARG, "unknown precision");
   if (opts->n_chains < 1 || opts->n_chains > 8) return fail(nullptr, TNMC_ERR_ARG, "n_chains must be in [1, 8]");
   for (int k = 0; k < n_real; ++k)
@@ -281,6 +287,7 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
   TRY(dalloc(c, &c->logz, z.logz));
   TRY(dalloc(c, &c->rowbuf, z.rowbuf));
   TRY(dalloc(c, &c->Rstore, z.Rstore));
+  if (z.mscratch) TRY(dalloc(c, &c->mscratch, z.mscratch));
   TRY(dalloc(c, &c->stats, z.stats));
   TRY(dalloc(c, &c->status, z.status));
   TRY(dalloc(c, &c->rstatus, z.rstatus));
@@ -395,12 +402,14 @@ tnmc_status tnmc_build_env(tnmc_ctx* c, double* log_z_host) {
     case TNMC_MIXED_BF16: {
       tnmc::EnvBuildArgs<float, __nv_bfloat16> a{c->L, c->n_real, c->chi, c->J, c->beta, (__nv_bfloat16*)c->env, c->kdim,
                                                  c->dqr, c->lam, c->logz, (float*)c->rowbuf, (float*)c->Rstore, c->stats, c->status};
+      a.Mscratch = (float*)c->mscratch;
       e = tnmc::launch_env_build(a, c->CHI, c->stream);
       break;
     }
     default: {
       tnmc::EnvBuildArgs<float, float> a{c->L, c->n_real, c->chi, c->J, c->beta, (float*)c->env, c->kdim, c->dqr,
                                          c->lam, c->logz, (float*)c->rowbuf, (float*)c->Rstore, c->stats, c->status};
+      a.Mscratch = (float*)c->mscratch;
       e = tnmc::launch_env_build(a, c->CHI, c->stream);
     }
   }
@@ -626,7 +635,8 @@ tnmc_status tnmc_env_build_occupancy(int L, int chi, int precision, int32_t* cta
   if (!ctas_per_sm || L < 2 || L > 4096 || precision < 0 || precision > 3)
     return fail(nullptr, TNMC_ERR_ARG, "bad arguments");
   const int CHI = round_chi(chi);
-  if (chi < 1 || CHI == 0) return fail(nullptr, TNMC_ERR_UNSUPPORTED, "chi outside 1..32");
+  if (chi < 1 || CHI == 0 || (CHI > 32 && precision == TNMC_FP64))
+    return fail(nullptr, TNMC_ERR_UNSUPPORTED, "chi outside 1..64 (1..32 in FP64)");
   int per_sm = 0, dev = 0, sms = 0;
   cudaError_t e = tnmc::env_build_occupancy(L, CHI, precision, &per_sm);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -646,6 +656,7 @@ size_t tnmc_device_bytes(const tnmc_ctx* c) {
 
 size_t tnmc_estimate_device_bytes(int L, int n_real, int chi, const tnmc_opts* opts, int n_max) {
   if (L < 2 || n_real < 1 || !opts || n_max < 0 || round_chi(chi) == 0) return 0;
+  if (chi > 32 && opts->precision == TNMC_FP64) return 0;
   if (opts->n_chains < 1 || opts->n_chains > 8) return 0;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||

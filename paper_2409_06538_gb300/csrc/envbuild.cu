@@ -118,7 +118,8 @@ template <int CHI> struct EnvCfg {
   static constexpr int D = 2 * CHI;                 // MPO bond x MPS bond
   // 8 lanes per Jacobi pair (8*CHI threads); CHI = 32 runs 256 threads so that three
   // realizations fit on one SM in FP32 (80 registers, 72 KB of shared memory each)
-  static constexpr int NWARP = CHI < 4 ? 4 : (CHI > 8 ? 8 : CHI);
+  // CHI = 64 runs 512 threads (64 Jacobi pairs) with one CTA per SM
+  static constexpr int NWARP = CHI > 32 ? 16 : (CHI < 4 ? 4 : (CHI > 8 ? 8 : CHI));
   static constexpr int NT = 32 * NWARP;
   static constexpr int TILE = 2 * CHI * CHI;        // [y][alpha][beta]
 };
@@ -133,6 +134,9 @@ template <typename T, int CHI> struct JStride {
 
 template <typename T, int CHI>
 __host__ __device__ constexpr size_t env_smem_elems() {
+  // CHI = 64: only Y and V (D*DP each) and the Householder vectors (4D) stay in shared memory;
+  // M lives in per-realization global scratch and R, the tile are read from global memory
+  if (CHI > 32) return (size_t)2 * (2 * CHI) * JStride<T, CHI>::DP + (size_t)4 * (2 * CHI);
   // backward: M, R (D*D each), Y, V (D*DP each) + tile (2*CHI*CHI); P (D*CHI) lives in the Y
   //           region and Q (2*CHI*CHI) in the V region between their uses
   // forward : X (2D*D, aliases M and Y) + R (D*D) + tile; the Householder vectors use V
@@ -151,7 +155,7 @@ template <int CHI> struct Pair {
 };
 
 template <typename T, typename TE, int CHI>
-__global__ void __launch_bounds__(EnvCfg<CHI>::NT, sizeof(T) == 8 ? 1 : 3)
+__global__ void __launch_bounds__(EnvCfg<CHI>::NT, (sizeof(T) == 8 || CHI > 32) ? 1 : 3)
 env_build_kernel(EnvBuildArgs<T, TE> args) {
   using C = EnvCfg<CHI>;
   constexpr int D = C::D, NWARP = C::NWARP, NT = C::NT, TILE = C::TILE;
@@ -163,13 +167,17 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
+  // CHI = 64 (kBig): M in global scratch, R_c and the previous-row tile read from global
+  // memory where they are stored (the pointers move with the site), shared memory for Y, V
+  constexpr bool kBig = CHI > 32;
+  T* const Rstore_r = args.Rstore + (size_t)real * args.L * D * D;
   // backward-phase layout
   constexpr int DP = JStride<T, CHI>::DP;
-  T* Mc = sm;                 // D x D   col-major, compact columns j = x*kn + g
-  T* Yc = Mc + D * D;         // n columns of stride DP (rows >= D zero)
+  T* Mc = kBig ? args.Mscratch + (size_t)real * D * D : sm;   // D x D col-major, columns j = x*kn + g
+  T* Yc = kBig ? sm : Mc + D * D;  // n columns of stride DP (rows >= D zero)
   T* Vc = Yc + D * DP;        // n columns of stride DP (rows >= n zero)
-  T* Rc = Vc + D * DP;        // D x D   col-major R_c
-  T* Bt = Rc + D * D;         // previous-row tile [y][al][be]
+  T* Rc = kBig ? Rstore_r : Vc + D * DP;   // D x D col-major R_c
+  T* Bt = kBig ? nullptr : Rc + D * D;     // previous-row tile [y][al][be]
   // P is written after the SVD (Y is dead by then) and read by the next site's Q = B P before
   // that site's Y is formed; Q is written after this site's V is dead and read before the next
   // V is initialised: so P takes the Y region and Q the V region
@@ -179,12 +187,12 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
   T* Xs = sm;                 // 2D x D col-major
 
   __shared__ T Wc[8];               // W[x][a][b] at x*4 + a*2 + b
-  int8_t* jv_s = reinterpret_cast<int8_t*>(Bt + TILE);        // Jv[r][c], L entries
+  int8_t* jv_s = reinterpret_cast<int8_t*>(kBig ? Vc + D * DP + 4 * D : Bt + TILE);   // Jv[r][c], L entries
   int8_t* jh_s = jv_s + args.L;                                // Jh[r+1][c], L-1 entries
   const T eb = (T)exp(beta), ebm = (T)exp(-beta);             // exp(+-beta): every Boltzmann weight
-  T (*vbuf)[2 * D] = reinterpret_cast<T (*)[2 * D]>(Vc);   // Householder vectors (double-
-                                                            // buffered; the V region is idle
-                                                            // in the forward sweep)
+  // Householder vectors (double-buffered; the V region is idle in the forward sweep unless
+  // the forward matrix X fills Y and V, as for kBig)
+  T (*vbuf)[2 * D] = reinterpret_cast<T (*)[2 * D]>(kBig ? Vc + D * DP : Vc);
   __shared__ T vcoef[2];
   __shared__ T red[32];
   __shared__ T sig[D];
@@ -246,16 +254,21 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       }
     };
     // R_0 = [1]
+    if constexpr (kBig) Rc = Rstore;
     for (int e = tid; e < D * D; e += NT) Rc[e] = (e == 0) ? T(1) : T(0);
-    if (tid == 0) {
+    if (!kBig && tid == 0) {
       for (int e = 0; e < D * D; ++e) Rstore[e] = (e == 0) ? T(1) : T(0);
     }
-    prefetch_async(Bt, prev, TILE * (int)sizeof(T), tid, NT);      // tile of site 0
+    if constexpr (!kBig) prefetch_async(Bt, prev, TILE * (int)sizeof(T), tid, NT);      // tile of site 0
     __syncthreads();
 
     // ---------------- forward sweep: R factors of the left parts ----------------
     for (int c = 0; c < L - 1; ++c) {
       set_w(c);
+      if constexpr (kBig) {
+        Rc = Rstore + (size_t)c * D * D;
+        Bt = const_cast<T*>(prev + (size_t)c * TILE);
+      }
       cp_async_wait_env();
       __syncthreads();
       // X[(x,i),(b,be)] = sum_al (W(x,0,b) R[i][al] + W(x,1,b) R[i][CHI+al]) B[b][al][be]:
@@ -287,7 +300,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       }
       __syncthreads();
       // the next site's tile streams in while the QR runs
-      prefetch_async(Bt, prev + (size_t)(c + 1) * TILE, TILE * (int)sizeof(T), tid, NT);
+      if constexpr (!kBig) prefetch_async(Bt, prev + (size_t)(c + 1) * TILE, TILE * (int)sizeof(T), tid, NT);
       // Householder QR of X (m = 2D rows, D columns); warp (j % NWARP) owns column j.
       constexpr int m = 2 * D;
       const T tiny = (sizeof(T) == 4) ? T(1e-36) : T(1e-300);
@@ -381,7 +394,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       for (int e = tid; e < D * D; e += NT) {
         const int i = e % D, j = e / D;
         const T v = (i <= j) ? Xs[(size_t)j * m + i] * inv : T(0);
-        Rc[e] = v;
+        if constexpr (!kBig) Rc[e] = v;      // kBig reads R_{c+1} back from Rstore
         Rout[e] = v;
       }
       __syncthreads();
@@ -400,6 +413,10 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
     for (int c = L - 1; c >= 0; --c) {
       // Bt (tile c) and Rc (R_c) were prefetched during the previous site
       set_w(c);
+      if constexpr (kBig) {
+        Rc = Rstore + (size_t)c * D * D;
+        Bt = const_cast<T*>(prev + (size_t)c * TILE);
+      }
       cp_async_wait_env();
       __syncthreads();
       // Q[b][al][g] = sum_be B[b][al][be] P[(b,be)][g]: 4 x 4 register tiles
@@ -432,7 +449,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
         }
       }
       __syncthreads();
-      if (c > 0) prefetch_async(Bt, prev + (size_t)(c - 1) * TILE, TILE * (int)sizeof(T), tid, NT);
+      if (!kBig && c > 0) prefetch_async(Bt, prev + (size_t)(c - 1) * TILE, TILE * (int)sizeof(T), tid, NT);
       const int n = 2 * kn;    // compact columns j = x*kn + g
       // M[(a,al)][j] = sum_b W(x,a,b) Q[b][al][g]
       for (int e = tid; e < D * n; e += NT) {
@@ -515,7 +532,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       __syncthreads();
       const T tinyY = red[NWARP] * num<T>::eps * num<T>::eps;
       // R_{c-1} streams in while the SVD runs (Rc is not read again at this site)
-      if (c > 1) prefetch_async(Rc, Rstore + (size_t)(c - 1) * D * D, D * D * (int)sizeof(T), tid, NT);
+      if (!kBig && c > 1) prefetch_async(Rc, Rstore + (size_t)(c - 1) * D * D, D * D * (int)sizeof(T), tid, NT);
       const T tol = jacobi_tol<T, D>();
       // One-sided Jacobi in a block-cyclic order.  The npad columns form NB = npad/4 blocks of
       // four; in each block-round (a round-robin over blocks) warp wj owns one block pair and
@@ -690,6 +707,55 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
   }
 
   // log Z = sum_r lam_r + log sum_x prod_c exp(beta Jh[0][c] s_c s_{c+1}) Gt_0(x)
+  if constexpr (kBig) {
+    // as below, each lane holding the bond indices lane + 32 e of the running vector
+    constexpr int E = CHI / 32;
+    if (warp == 0) {
+      const T* row0 = rowbuf;
+      double ell[2][E];
+      double lsum = 0.0;
+      for (int x = 0; x < 2; ++x)
+        for (int e = 0; e < E; ++e) ell[x][e] = (double)row0[x * CHI * CHI + 0 * CHI + lane + 32 * e];
+      for (int c = 1; c < L; ++c) {
+        const T* t = row0 + (size_t)c * TILE;
+        const double jb = beta * (double)Jh[c - 1];
+        double nx[2][E];
+        for (int x = 0; x < 2; ++x)
+          for (int e = 0; e < E; ++e) nx[x][e] = 0.0;
+        double f0[2], f1[2];
+        for (int x = 0; x < 2; ++x) { f0[x] = exp(jb * spin_of(0) * spin_of(x)); f1[x] = exp(jb * spin_of(1) * spin_of(x)); }
+        for (int h = 0; h < E; ++h)
+          for (int j = 0; j < 32; ++j) {
+            const int al = 32 * h + j;
+            const double l0 = __shfl_sync(0xffffffffu, ell[0][h], j);
+            const double l1 = __shfl_sync(0xffffffffu, ell[1][h], j);
+            for (int x = 0; x < 2; ++x) {
+              const double cf = f0[x] * l0 + f1[x] * l1;
+              for (int e = 0; e < E; ++e) nx[x][e] += cf * (double)t[x * CHI * CHI + al * CHI + lane + 32 * e];
+            }
+          }
+        double mx = 0.0;
+        for (int x = 0; x < 2; ++x)
+          for (int e = 0; e < E; ++e) mx = fmax(mx, fabs(nx[x][e]));
+        mx = warp_max(mx);
+        for (int x = 0; x < 2; ++x)
+          for (int e = 0; e < E; ++e) ell[x][e] = mx > 0.0 ? nx[x][e] / mx : nx[x][e];
+        if (mx > 0.0) lsum += log(mx);
+      }
+      const double tot = __shfl_sync(0xffffffffu, ell[0][0] + ell[1][0], 0);
+      if (lane == 0) {
+        double s = 0.0;
+        for (int rr = 0; rr < L; ++rr) s += lam[rr];
+        args.logz[real] = s + lsum + log(tot);
+        if (args.stats) {
+          args.stats[real * 4 + 0] = max_sweeps_seen;
+          args.stats[real * 4 + 1] = unconverged;
+          args.stats[real * 4 + 2] = total_sweeps;
+          args.stats[real * 4 + 3] = n_svd;
+        }
+      }
+    }
+  } else {
   if (warp == 0) {
     const T* row0 = rowbuf;   // row 0 lives in buffer (0 & 1) = 0
     double ell[2];            // lane holds ell[x][lane] for lane < CHI
@@ -726,6 +792,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       }
     }
   }
+  }
 }
 
 template <typename T, typename TE, int CHI>
@@ -747,6 +814,9 @@ cudaError_t launch_env_build(const EnvBuildArgs<T, TE>& a, int CHI, cudaStream_t
     case 8: return launch_env_build_t<T, TE, 8>(a, st);
     case 16: return launch_env_build_t<T, TE, 16>(a, st);
     case 32: return launch_env_build_t<T, TE, 32>(a, st);
+    case 64:
+      if constexpr (sizeof(T) == 4) return launch_env_build_t<T, TE, 64>(a, st);  // FP64 does not fit
+      return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
@@ -772,6 +842,9 @@ cudaError_t env_build_occupancy(int L, int CHI, int precision, int* per_sm) {
     case 8: return occupancy_t<T, TE, 8>(L, per_sm);              \
     case 16: return occupancy_t<T, TE, 16>(L, per_sm);            \
     case 32: return occupancy_t<T, TE, 32>(L, per_sm);            \
+    case 64:                                                      \
+      if constexpr (sizeof(T) == 4) return occupancy_t<T, TE, 64>(L, per_sm); \
+      return cudaErrorInvalidValue;                               \
     default: return cudaErrorInvalidValue;                        \
   }
   if (precision == 0) { TNMC_OCC(double, double) }
@@ -787,6 +860,7 @@ size_t env_build_smem_bytes(int CHI, bool fp64) {
     case 8: return env_smem_elems<float, 8>() * el;
     case 16: return env_smem_elems<float, 16>() * el;
     case 32: return env_smem_elems<float, 32>() * el;
+    case 64: return fp64 ? 0 : env_smem_elems<float, 64>() * el;
     default: return 0;
   }
 }

@@ -28,6 +28,7 @@ struct EnvBuildArgs {
   T* Rstore;              // [real][L][D*D] scratch
   long long* stats;       // [real][4]: max Jacobi sweeps, unconverged SVDs, total sweeps, SVDs (nullable)
   unsigned* status;
+  T* Mscratch = nullptr;  // [real][D*D] scratch, used only when CHI = 64 (M does not fit in shared memory)
 };
 
 template <typename T, typename TE>

@@ -502,10 +502,11 @@ tnmc_status tnmc_server_create(const tnmc_server_opts* opts, tnmc_server** out) 
 tnmc_status tnmc_server_submit(tnmc_server* s, const tnmc_request* req, int64_t* id_out) {
   if (!s || !req || !id_out) return TNMC_ERR_ARG;
   const tnmc_request& r = *req;
-  if (r.L < 2 || r.L > 4096 || r.chi < 1 || r.chi > 32 || !(r.p >= 0.0 && r.p <= 1.0) ||
+  const int chi_max = s->opts.precision == TNMC_FP64 ? 32 : 64;
+  if (r.L < 2 || r.L > 4096 || r.chi < 1 || r.chi > chi_max || !(r.p >= 0.0 && r.p <= 1.0) ||
       !(r.beta > 0.0) || !std::isfinite(r.beta) || r.n_samples < 1) {
     std::lock_guard<std::mutex> lk(s->mu);
-    s->err = "request: need 2 <= L <= 4096, 1 <= chi <= 32, 0 <= p <= 1, finite beta > 0, n_samples >= 1";
+    s->err = "request: need 2 <= L <= 4096, 1 <= chi <= 64 (32 in FP64), 0 <= p <= 1, finite beta > 0, n_samples >= 1";
     return TNMC_ERR_ARG;
   }
   {

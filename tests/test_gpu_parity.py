@@ -66,10 +66,35 @@ def test_exact_when_untruncated(tn, precision):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "tf32"])
+def test_exact_when_untruncated_chi64(tn, precision):
+    """chi = 64 = 2^{L/2} at L = 12: nothing is truncated, so the GPU log Z equals the oracle's
+    and every proposal has log q = -beta E - log Z (the chi = 64 build keeps M in global
+    scratch and reads R and the tiles from global memory; the sampler holds two bond indices
+    per lane)."""
+    p, L, chi = 0.10, 12, 64
+    beta = lattice.nishimori_beta(p)
+    seeds = [1, 5]
+    ctx = _ctx(tn, L, p, chi, seeds, precision)
+    lz = ctx.build_env()
+    out = ctx.propose(20, 0)
+    ctx.accept()
+    lq = out["logq"].cpu().numpy()
+    E = out["energy"].cpu().numpy()
+    for k, s in enumerate(seeds):
+        env = oracle_envs(s, L, p, chi)
+        assert abs(lz[k] - env.log_z) < 1e-4 * abs(env.log_z)
+        resid = lq[k] + beta * E[k] + env.log_z
+        assert np.abs(resid).max() < 5e-3
+    assert np.all(ctx.realization_status() == 0)
+    ctx.close()
+
+
 @pytest.mark.parametrize("precision,L,chi,p", [
     ("fp64", 16, 8, 0.109), ("fp64", 24, 16, 0.109), ("fp64", 13, 5, 0.2),
     ("fp32", 16, 8, 0.109), ("fp32", 24, 16, 0.109),
     ("tf32", 24, 16, 0.109), ("tf32", 20, 32, 0.109), ("tf32", 40, 32, 0.109),
+    ("fp32", 16, 64, 0.109), ("tf32", 20, 64, 0.109),
 ])
 def test_conditionals_and_spins(tn, precision, L, chi, p):
     """Per-site q(+) teacher-forced on the GPU's spins; log q; the spins themselves equal the

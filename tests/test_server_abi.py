@@ -82,9 +82,14 @@ def test_estimate_follows_the_allocation_formulas(lib):
     # proposal buffers: packed spins + log q + energy + magnetisation + current index
     words = (L * L + 31) // 32
     assert est(L, 1, chi, 10) - one == 2 * 10 * (4 * words + 8 + 4 + 4 + 4)
-    # chi is rounded up to the compiled tile (8 here); > 32 and bad arguments give 0
+    # chi is rounded up to the compiled tile (8 here); FP64 above 32, any path above 64 and bad
+    # arguments give 0; chi = 64 in FP32 adds the M scratch of the environment build
     assert est(L, 1, 7, 0) == one
     assert est(L, 1, 33, 0) == 0 and est(1, 1, chi, 0) == 0 and est(L, 0, chi, 0) == 0
+    o32 = _capi.Opts(_capi.PRECISIONS["fp32"], 2, 0, None)
+    e64 = lib.tnmc_estimate_device_bytes(L, 1, 64, ctypes.byref(o32), 0)
+    assert e64 >= L * L * 2 * 64 * 64 * 4 + 128 * 128 * 4
+    assert lib.tnmc_estimate_device_bytes(L, 1, 65, ctypes.byref(o32), 0) == 0
 
 
 def test_server_refuses_bad_options_without_a_device(lib):
