@@ -50,7 +50,7 @@ typedef enum {
   TNMC_ERR_NUMERIC = 4,     /* w(+)+w(-) <= 0 or not finite at some site (oracle reading: error) */
   TNMC_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
   TNMC_ERR_STATE = 6,       /* call out of order (e.g. propose before build_env) */
-  TNMC_ERR_UNSUPPORTED = 7  /* configuration not built into this library (e.g. chi > 32) */
+  TNMC_ERR_UNSUPPORTED = 7  /* configuration not built into this library (e.g. chi > 64, or > 32 in FP64) */
 } tnmc_status;
 
 typedef enum {
