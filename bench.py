@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean arrivals per second")
     ap.add_argument("--serve-Ls", default="16,32,64,128,256,512")
-    ap.add_argument("--serve-chi-max", type=int, default=32)
+    ap.add_argument("--serve-chi-max", type=int, default=64)
     ap.add_argument("--serve-inflight", type=int, default=32)
     ap.add_argument("--serve-linger-ms", type=float, default=20.0)
     return ap.parse_args()
