@@ -11,12 +11,12 @@ of row r is the sum over every spin below row r,
 
 which is the row-transfer MPO (bond 2: the T tensors of Sec. II.B with the copy tensor
 delta and the Boltzmann matrices W absorbed) applied to the MPS of G_{r+1}.  The bond
-dimension doubles and is cut back to D = chi "by using the SVD" (Sec. II.B): a
+dimension doubles and is cut back to D = chi by singular value decomposition (Sec. II.B): a
 left-to-right Householder-QR sweep brings the MPS to left-canonical form, then a
 right-to-left SVD sweep keeps at every bond the min(chi, rows, cols) largest singular
 values (no tolerance cut).  The result is stored normalised, G_r ~ exp(Lambda_r) Gt_r
-with Lambda_r = sum_{r' >= r} lam[r'], and every row is cached for the sampler
-("the process tensors are stored ... for later use", Sec. II.B).
+with Lambda_r = sum_{r' >= r} lam[r'], and every row is kept for the sampler, which reuses
+the cached process tensors (Sec. II.B).
 
 Site tensors are arrays B[c] of shape (k_c, 2, k_{c+1}); physical index 0 <-> s=+1.
 """

@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Proposals are independent draws from q (Sec. II.B: "configurations generated in this way
-are independent"), so g(s'|s) = q(s') and Eq. (accptanceratio) becomes
+Proposals are independent draws from q (Sec. II.B: each proposal is sampled afresh from the
+environments, with no dependence on the current state), so g(s'|s) = q(s') and
+Eq. (accptanceratio) becomes
     p_a(s'|s) = min{1, q(s) P(s') / (q(s') P(s))}
               = min{1, exp([-beta E(s') - log q(s')] - [-beta E(s) - log q(s)])},
 the form App. A works through for the 1D ring.  Readings where the paper is silent:
