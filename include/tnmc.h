@@ -47,18 +47,20 @@ typedef enum {
   TNMC_ERR_ARG = 1,         /* invalid argument (sizes, NULL where not allowed, |J| != 1, ...) */
   TNMC_ERR_OOM = 2,         /* device allocation failed */
   TNMC_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
-  TNMC_ERR_NUMERIC = 4,     /* w(+)+w(-) <= 0 or not finite at some site (oracle reading: error) */
+  TNMC_ERR_NUMERIC = 4,     /* w(+)+w(-) <= 0 after clamping, or not finite, at some site */
   TNMC_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
   TNMC_ERR_STATE = 6,       /* call out of order (e.g. propose before build_env) */
   TNMC_ERR_UNSUPPORTED = 7  /* configuration not built into this library (e.g. chi > 64, or > 32 in FP64) */
 } tnmc_status;
 
 typedef enum {
-  TNMC_FP64 = 0,        /* everything in FP64 */
-  TNMC_FP32 = 1,        /* environments built and stored in FP32, sampling in FP32 */
-  TNMC_MIXED_BF16 = 2,  /* FP32 build, BF16 cached environments, BF16 tensor-core sampling
-                           GEMMs with FP32 accumulation; log-norms and log q in FP64 */
-  TNMC_MIXED_TF32 = 3   /* FP32 build and cache, TF32 tensor-core sampling GEMMs */
+  TNMC_FP64 = 0,        /* everything in FP64 (chi <= 32) */
+  TNMC_FP32 = 1,        /* environments built and stored in FP32, sampling in FP32 (FMA) */
+  TNMC_MIXED_BF16 = 2,  /* FP32 build, BF16 cached environments read into FP32 sampling (FMA);
+                           outside the 1e-3 conditional tolerance (measured, see the tests) */
+  TNMC_MIXED_TF32 = 3   /* FP32 build and cache; sampling products on the tensor cores as
+                           3xTF32 (FP32 accuracy) for chi = 16 and 32, FP32 FMA otherwise.
+                           Every path keeps log-norms, log q and the Metropolis test in FP64. */
 } tnmc_precision;
 
 typedef struct {
@@ -98,8 +100,8 @@ tnmc_status tnmc_couplings_pmj(int L, int n_real, const uint64_t* seeds_host, do
                                int8_t* out_dev, void* stream);
 
 /* Create a context for n_real independent disorder realizations of one lattice size L
- * and one cut-off bond dimension chi (the "cutoff bond dimension of the matrix product
- * states", D in Table tableparameter).
+ * and one cut-off bond dimension chi (the largest bond dimension the boundary MPS keeps,
+ * D in Table tableparameter).
  *   couplings : host or device, n_real * 2L(L-1) int8 +-1 (copied);
  *   beta_host : n_real inverse temperatures (Eq. P); on the Nishimori line
  *               beta = 0.5 ln((1-p)/p) (Sec. III.A);
