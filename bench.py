@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -161,7 +162,8 @@ class Clocks:
     def __init__(self, dev):
         self.dev = dev
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="tnmc_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
@@ -175,6 +177,10 @@ class Clocks:
 
     def stop(self):
         if self.p is None:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
             return None
         self.p.terminate()
         try:
@@ -198,6 +204,10 @@ class Clocks:
         if not sm:
             return None
         load = [x for x in sm if x > 0.5 * mx] or sm
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         return dict(sm_mhz=statistics.median(load), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
 
 

@@ -1,6 +1,6 @@
 """Acceptance probability p_a of the tensor-network proposals against lattice size, bond
-dimension and temperature on the Nishimori line (Sec. III.C "Acceptance ratio of TNMC",
-Fig. fig:pa): for every (L, chi, p) it builds the environments of R seeded realizations,
+dimension and temperature on the Nishimori line (Sec. III.B, acceptance of the tensor-network
+proposals, Fig. fig:pa): for every (L, chi, p) it builds the environments of R seeded realizations,
 draws n proposals per chain (two chains) and runs the Metropolis filter, then prints one JSON
 line with p_a = accepted / proposed (each chain's unconditional first state excluded), its
 standard error over realizations, tau ~ 1/p_a and the wall time.  Realizations whose proposals
