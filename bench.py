@@ -212,6 +212,34 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- our arm
+def run_waves(steps, S, streams, make_event, inputs, work, marks=None):
+    """Queue the batches `steps` (global step indices) on S contexts and streams, in waves of
+    S.  A wave first queues every batch's new inputs (small kernels) on its stream, then every
+    stream of the wave waits for all of them before its environment build: the builds of a wave
+    are dispatched together onto SMs that no small kernel of another stream occupies.  (With
+    the build filling 448 of 456 CTA slots, a couplings kernel resident on an SM when the builds
+    are dispatched can keep a build CTA waiting for a whole build to finish elsewhere.)
+    inputs(k, i) queues batch k's inputs on context i; work(i, marks) queues the rest;
+    marks[j] (optional) are four timing events of the j-th batch, the first recorded here."""
+    steps = list(steps)
+    for w0 in range(0, len(steps), S):
+        wave = steps[w0:w0 + S]
+        ready = []
+        for j, k in enumerate(wave):
+            i = (w0 + j) % S
+            if marks is not None:
+                marks[w0 + j][0].record(streams[i])
+            inputs(k, i)
+            e = make_event()
+            e.record(streams[i])
+            ready.append(e)
+        for j, k in enumerate(wave):
+            i = (w0 + j) % S
+            for e in ready:
+                streams[i].wait_event(e)
+            work(i, marks[w0 + j] if marks is not None else None)
+
+
 def main():
     a = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -260,12 +288,13 @@ def main():
                     n_therm=0, stream=streams[i]) for i in range(S)]
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
-    def enqueue(step, i, marks=None):
-        """One step on context i: new realizations (couplings generated on the device),
-        environments, proposals, Metropolis -- all queued on stream i, no host sync."""
+    def inputs(step, i):
+        """New realizations on context i: couplings generated on the device, queued on stream i."""
+        ctxs[i].set_realizations(seeds_for(step), [beta] * R, a.p)
+
+    def work(i, marks=None):
+        """Environments, proposals, Metropolis on context i -- queued on stream i, no host sync."""
         ctx, st = ctxs[i], streams[i]
-        if marks: marks[0].record(st)
-        ctx.set_realizations(seeds_for(step), [beta] * R, a.p)
         ctx.build_env(return_logz=False)
         if marks: marks[1].record(st)
         ctx.propose(a.n, 0, outputs=False)
@@ -273,8 +302,8 @@ def main():
         ctx.accept()
         if marks: marks[3].record(st)
 
-    for w in range(a.warmup):
-        enqueue(w, w % S)
+    sync_ev = lambda: torch.cuda.Event()  # noqa: E731
+    run_waves(range(a.warmup), S, streams, sync_ev, inputs, work)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -287,11 +316,8 @@ def main():
     t_start.record(main_st)
     for st in streams:
         st.wait_event(t_start)
-    marks = []
-    for k in range(a.steps):
-        m = [ev() for _ in range(4)]
-        enqueue(a.warmup + k, k % S, m)
-        marks.append(m)
+    marks = [[ev() for _ in range(4)] for _ in range(a.steps)]
+    run_waves(range(a.warmup, a.warmup + a.steps), S, streams, sync_ev, inputs, work, marks)
     for st in streams:
         e = ev(); e.record(st); main_st.wait_event(e)
     t_end.record(main_st)
