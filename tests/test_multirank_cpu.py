@@ -21,7 +21,7 @@ def _free_port():
 def _fake_obs(seed):
     """Per-realization thermal means standing in for one realization's run (host data only)."""
     r = np.random.default_rng(int(seed))
-    keys = ["E", "E2", "m_abs", "m2", "m4", "q", "q_abs", "q2", "q4"]
+    keys = ["E", "E2", "m_abs", "m2", "m4", "q", "q_abs", "q2", "q4", "m_edge", "m_edge_abs", "m_edge2"]
     d = {k: float(r.random()) for k in keys}
     d.update(n_acc=int(r.integers(0, 100)), n_prop=100, clamps=0)
     return d
@@ -34,10 +34,10 @@ def _worker(rank, world, port, seeds, out_path):
     from paper_2409_06538_gb300 import shard
     dist.init_process_group("gloo", rank=rank, world_size=world)
     mine = shard.shard_seeds(seeds, rank, world)
-    avg, n = shard.gather_disorder_average([_fake_obs(s) for s in mine])
+    avg, n = shard.gather_disorder_average([_fake_obs(s) for s in mine], L=16, beta=0.9)
     if rank == 0:
         np.save(out_path, np.array([avg["E"][0], avg["E"][1], avg["m2"][0], avg["U_m"], avg["Q_q"],
-                                    avg["acceptance"], n], dtype=np.float64))
+                                    avg["acceptance"], n, avg["chi_q"], avg["chi_edge"]], dtype=np.float64))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -58,6 +58,7 @@ def test_gloo_two_ranks_reproduce_single_process(tmp_path):
     out = str(tmp_path / "avg.npy")
     mp.spawn(_worker, args=(2, _free_port(), seeds, out), nprocs=2, join=True)
     got = np.load(out)
-    ref = disorder_average([_fake_obs(s) for s in seeds])
-    want = np.array([ref["E"][0], ref["E"][1], ref["m2"][0], ref["U_m"], ref["Q_q"], ref["acceptance"], len(seeds)])
+    ref = disorder_average([_fake_obs(s) for s in seeds], 16, 0.9)
+    want = np.array([ref["E"][0], ref["E"][1], ref["m2"][0], ref["U_m"], ref["Q_q"], ref["acceptance"], len(seeds),
+                     ref["chi_q"], ref["chi_edge"]])
     assert np.allclose(got, want, rtol=0, atol=1e-12)
