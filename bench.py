@@ -149,7 +149,7 @@ def _config(a):
     return dict(workload=f"TNMC L={a.L} chi={a.chi} p={a.p} Nishimori beta, {a.R} realizations x "
                          f"{a.chains} chains x {a.n} proposals per GPU per step",
                 L=a.L, chi=a.chi, p=a.p, realizations_per_gpu=a.R, chains=a.chains,
-                proposals_per_chain=a.n, precision=a.precision,
+                proposals_per_chain=a.n, precision=("fp64" if a.impl == "reference" else a.precision),
                 l2="inputs larger than L2: the environment cache read by the sampler is rebuilt every step")
 
 
@@ -265,6 +265,8 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     import paper_2409_06538_gb300 as tn
+    from paper_2409_06538_gb300 import _capi
+    import ctypes
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -288,9 +290,15 @@ def main():
                     n_therm=0, stream=streams[i]) for i in range(S)]
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
+    # per timed batch, the realizations' failure flags (copied on the device after the
+    # Metropolis step, read once at the end)
+    flags = torch.zeros((a.warmup + a.steps, R), dtype=torch.int32, device=dev)
+    step_of = {}
+
     def inputs(step, i):
         """New realizations on context i: couplings generated on the device, queued on stream i."""
         ctxs[i].set_realizations(seeds_for(step), [beta] * R, a.p)
+        step_of[i] = step
 
     def work(i, marks=None):
         """Environments, proposals, Metropolis on context i -- queued on stream i, no host sync."""
@@ -300,6 +308,7 @@ def main():
         ctx.propose(a.n, 0, outputs=False)
         if marks: marks[2].record(st)
         ctx.accept()
+        ctx.realization_status_async(flags[step_of[i]])
         if marks: marks[3].record(st)
 
     sync_ev = lambda: torch.cuda.Event()  # noqa: E731
@@ -349,16 +358,26 @@ def main():
     samp_union_ms = union([(m[1], m[2]) for m in marks])
     stats = [c.build_stats() for c in ctxs]
     mean_sweeps = sum(s_["total_sweeps"] for s_ in stats) / max(1, sum(s_["svds"] for s_ in stats))
-    obs = []
+    # realizations that met a doubly clamped site (TNMC_ERR_NUMERIC under the clamp reading):
+    # reported with their seeds, left out of the averages and of the throughput
+    fl = flags.cpu().numpy()
+    failed_seeds = [int(seeds_for(k)[r]) for k in range(a.warmup + a.steps) for r in range(R) if fl[k, r] != 0]
+    n_failed_timed = int((fl[a.warmup:] != 0).sum())
+    obs = []        # the last batch of every context (observables of the realizations it holds)
     for c in ctxs:
-        obs += c.observables()
+        obs += c.observables(allow_numeric=True)
     if world > 1:       # the one cross-rank exchange: per-realization means for [.] averages
         from paper_2409_06538_gb300 import shard
-        dav, _ = shard.gather_disorder_average(obs, L=L, beta=beta)
+        dav, _ = shard.gather_disorder_average(obs, L, beta)
     else:
         dav = tn.disorder_average(obs, L, beta)
     spins_per_step = R * a.chains * a.n * L * L
-    value = world * spins_per_step * a.steps / elapsed
+    spins_ok = (R * a.steps - n_failed_timed) * a.chains * a.n * L * L
+    if world > 1:
+        t = torch.tensor([spins_ok], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t)
+        spins_ok = float(t.item())
+    value = spins_ok / elapsed
 
     # ---- end to end through the public API with host buffers: one host thread per context,
     # each step copies its couplings from pinned host memory and reads its observables back
@@ -377,7 +396,8 @@ def main():
                 ctxs[i].build_env(return_logz=False)
                 ctxs[i].propose(a.n, 0, outputs=False)
                 ctxs[i].accept()
-                ctxs[i].observables()        # device-to-host read of the step's result
+                # device-to-host read of the step's result, per-realization status included
+                ctxs[i].observables(allow_numeric=True)
         t0 = time.perf_counter()
         ths = [threading.Thread(target=worker, args=(i,)) for i in range(S)]
         for th in ths:
@@ -391,7 +411,8 @@ def main():
             e_el = float(t.item())
         e2e = dict(value=world * spins_per_step * k_e2e / e_el, unit=UNIT,
                    h2d_bytes_per_step=int(R * 2 * L * (L - 1) + 16 * R),
-                   d2h_bytes_per_step=int(R * 112))
+                   d2h_bytes_per_step=int(R * (ctypes.sizeof(_capi.Obs) + 8)),
+                   note="every realization's spins counted (the couplings of step 0 are reused)")
 
     roof = roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps)
 
@@ -418,7 +439,14 @@ def main():
                     jacobi_mean_sweeps=mean_sweeps,
                     accepted_proposals_per_s=value / (L * L) * dav["acceptance"],
                     acceptance=dav["acceptance"], clamps=dav["clamps"],
-                    observables={k: dav[k] for k in ("E", "m2", "q2", "U_m", "Q_q", "m_edge2", "chi_q", "chi_edge")})
+                    failed_realizations=dict(
+                        timed=n_failed_timed, of=R * a.steps * world, seeds_rank0=failed_seeds,
+                        rule="realizations whose proposals met a site with w+ + w- <= 0 after clamping; "
+                             "their spins are not counted in value and their means not in the averages"),
+                    observables=dict({k: dav[k] for k in ("E", "m2", "q2", "U_m", "Q_q", "m_edge2", "chi_q",
+                                                          "chi_edge")},
+                                     realizations=dav["n_used"], dropped=dav["n_dropped"],
+                                     nishimori_E=-2 * L * (L - 1) * (1 - 2 * a.p)))
         print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()

@@ -63,12 +63,26 @@ typedef enum {
                            Every path keeps log-norms, log q and the Metropolis test in FP64. */
 } tnmc_precision;
 
+/* Device allocator of the caller (optional).  alloc(bytes, stream, user) returns device memory
+ * on the context's device, usable in stream order on `stream` (NULL on failure); free(ptr,
+ * bytes, stream, user) gives it back once the work queued on `stream` no longer needs it.  With
+ * both set, every device buffer of the context comes from them (PyTorch's caching allocator,
+ * a pool the application reserved up front, ...); with both NULL the library allocates with
+ * cudaMallocAsync (cudaMalloc where the device has no memory pools).  They are called only from
+ * tnmc_create, tnmc_propose (when it grows the proposal buffers), tnmc_eval_conditionals
+ * (without logq_dev) and tnmc_destroy, on the calling thread. */
+typedef void* (*tnmc_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*tnmc_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
 typedef struct {
   int precision;      /* tnmc_precision */
   int n_chains;       /* Markov chains (replicas) per realization, >= 1; the overlap q of
                          Sec. III.C is measured between chains 0 and 1 when n_chains >= 2 */
   int n_therm;        /* steps with global step index < n_therm are not measured */
   void* stream;       /* cudaStream_t for all work of this context; NULL = default stream */
+  tnmc_alloc_fn alloc;   /* caller's device allocator, or NULL (then free must be NULL too) */
+  tnmc_free_fn free;
+  void* alloc_user;      /* passed to alloc and free unchanged */
 } tnmc_opts;
 
 /* Per-realization thermal means over measured steps (Sec. III.C).  m = (1/N) sum_i s_i,
@@ -78,14 +92,51 @@ typedef struct {
  * and segment as printed); E, m and m_edge statistics pool all chains. */
 typedef struct {
   int64_t n_prop;       /* proposals processed by accept (all chains) */
-  int64_t n_acc;        /* proposals accepted (excluding each chain's unconditional first) */
+  int64_t n_acc;        /* Metropolis tests that accepted */
   int64_t n_meas;       /* measured (chain, step) pairs */
   int64_t n_meas_q;     /* measured steps for the overlap */
   int64_t clamps;       /* negative truncated weights clamped to zero while sampling */
   double E, E2, m_abs, m2, m4;
   double q, q_abs, q2, q4;
   double m_edge, m_edge_abs, m_edge2;
+  int64_t n_tests;      /* Metropolis tests: every proposal except each chain's first ever, which
+                           is its initial state; the acceptance rate is n_acc / n_tests */
+  int32_t status;       /* TNMC_OK, or TNMC_ERR_NUMERIC when a proposal of this realization met a
+                           site with w+ + w- not positive and finite (its means are then not
+                           valid samples of the clamp reading and tnmc_disorder_average skips it) */
+  int32_t reserved;
 } tnmc_obs;
+
+/* Disorder averages [.] over realizations (Sec. III.C): mean and standard error (sample
+ * standard deviation / sqrt(n_used)) of each thermal mean, in the order of tnmc_obs:
+ * E, E2, m_abs, m2, m4, q, q_abs, q2, q4, m_edge, m_edge_abs, m_edge2. */
+enum { TNMC_DIS_E = 0, TNMC_DIS_E2, TNMC_DIS_MABS, TNMC_DIS_M2, TNMC_DIS_M4, TNMC_DIS_Q, TNMC_DIS_QABS,
+       TNMC_DIS_Q2, TNMC_DIS_Q4, TNMC_DIS_MEDGE, TNMC_DIS_MEDGEABS, TNMC_DIS_MEDGE2, TNMC_DIS_N };
+typedef struct {
+  int32_t n_used;       /* realizations averaged (status TNMC_OK) */
+  int32_t n_dropped;    /* realizations left out because their status was not TNMC_OK */
+  double mean[TNMC_DIS_N], se[TNMC_DIS_N];
+  double U_m;           /* Binder ratio [<m^4>] / [<m^2>]^2 (Eq. eq:binderEA applied to m) */
+  double Q_q;           /* overlap Binder ratio [<q^4>] / [<q^2>]^2 (Eq. eq:binderEA, denominator read
+                           as the square of the disorder mean) */
+  double q2_sq;         /* [<q^2>^2], the other reading of that denominator */
+  double chi_q;         /* (L^2 / T) ([<q^2>] - [<q>]^2), Eq. eq:susEA as printed */
+  double chi_edge;      /* L [<m_edge^2>] (Sec. III.C) */
+  double acceptance;    /* sum n_acc / sum n_tests over the realizations used */
+  int64_t n_prop, n_tests, n_acc, clamps;   /* sums over the realizations used */
+} tnmc_disorder;
+
+/* Inverse temperature on the Nishimori line (Sec. III.A): exp(-2 beta) = p / (1 - p), i.e.
+ * beta = (1/2) ln((1-p)/p), written to *beta_out.  TNMC_ERR_ARG unless 0 < p < 1/2. */
+tnmc_status tnmc_nishimori_beta(double p, double* beta_out);
+
+/* Disorder averages of n_real per-realization thermal means (as tnmc_observables returns them)
+ * for lattice side L at inverse temperature beta (T = 1/beta in chi_q).  Realizations whose
+ * status is not TNMC_OK are skipped and counted in n_dropped.  Host code only: no device is
+ * needed.  Errors: TNMC_ERR_ARG for NULL pointers, n_real < 1, L < 2 or beta not positive and
+ * finite; TNMC_ERR_NUMERIC when no realization is usable (out then holds NaN means). */
+tnmc_status tnmc_disorder_average(const tnmc_obs* obs_host, int n_real, int L, double beta,
+                                  tnmc_disorder* out_host);
 
 typedef struct tnmc_ctx tnmc_ctx;
 
@@ -170,12 +221,14 @@ tnmc_status tnmc_eval_conditionals(tnmc_ctx* ctx, int n, const int8_t* spins_dev
 tnmc_status tnmc_accept(tnmc_ctx* ctx, uint8_t* accepted_dev, int64_t* n_accepted_host);
 
 /* Per-realization thermal means (host array of n_real tnmc_obs).  Synchronises.  Every
- * realization is filled in before the context's status is returned: on TNMC_ERR_NUMERIC the
- * realizations that tnmc_realization_status flags carry meaningless values and the others are
- * valid; on other errors nothing is meaningful. */
+ * realization is filled in, with its own status, before the context's status is returned: on
+ * TNMC_ERR_NUMERIC the realizations whose status field is TNMC_ERR_NUMERIC (the ones
+ * tnmc_realization_status flags) are not valid and the others are; on other errors nothing is
+ * meaningful. */
 tnmc_status tnmc_observables(tnmc_ctx* ctx, tnmc_obs* out_host);
 
-/* Reset chain states and observable accumulators (the environments stay cached). */
+/* Reset chain states, observable accumulators and the context's and every realization's
+ * device status word (the environments stay cached). */
 tnmc_status tnmc_reset_chains(tnmc_ctx* ctx);
 
 /* Release every device allocation of the context.  NULL is accepted. */
@@ -195,7 +248,8 @@ tnmc_status tnmc_copy_env(tnmc_ctx* ctx, int real, int row, double* tiles_host,
 
 /* Statistics of the last tnmc_build_env, summed over realizations: out_host[0] = most
  * Jacobi sweeps any truncation needed, [1] = truncations that hit the sweep limit,
- * [2] = total sweeps, [3] = truncating SVDs performed.  Synchronises. */
+ * [2] = total sweeps, [3] = truncating SVDs performed.  Synchronises; reports only CUDA
+ * errors (a sampling failure recorded in the status word is not the build's). */
 tnmc_status tnmc_build_stats(tnmc_ctx* ctx, int64_t* out_host);
 
 /* Environment build that allocates nothing.  The paper has no counterpart: this is a
@@ -221,9 +275,11 @@ tnmc_status tnmc_build_stats(tnmc_ctx* ctx, int64_t* out_host);
  * at the start of each call): calls whose work overlaps on the GPU race and corrupt each
  * other, so serialise them (one stream, or events).
  * Errors: TNMC_ERR_ARG for bad sizes or NULL buffers, and when the scratch this build needs,
- * n_real * ((2*L*2*C*C + L*4*C*C) * w + 4*(L+1)) bytes plus alignment (w = 8 for FP64, 4
- * otherwise), exceeds the 32 MiB array; TNMC_ERR_UNSUPPORTED for chi > 32; TNMC_ERR_CUDA
- * for a failed launch.  Device-side status is not returned (no synchronisation). */
+ * n_real * ((2*L*2*C*C + L*4*C*C) * w + 4*(L+1) + 32) + 4 bytes, each of its five parts
+ * rounded up to 256 bytes (w = 8 for FP64, 4 otherwise; 32 bytes of statistics per realization
+ * and one status word), exceeds the 32 MiB array; TNMC_ERR_UNSUPPORTED for chi > 32;
+ * TNMC_ERR_CUDA for a failed launch.  The build has no device-side failure to report, and the
+ * call does not synchronise. */
 tnmc_status tnmc_build_env_noalloc(int L, int n_real, int chi, int precision,
                                    const int8_t* couplings_dev, const double* beta_dev,
                                    void* env_dev, int32_t* kdim_dev, double* lam_dev,
@@ -235,6 +291,12 @@ tnmc_status tnmc_build_env_noalloc(int L, int n_real, int chi, int precision,
  * Cleared by tnmc_reset_chains (and so by tnmc_set_couplings / tnmc_set_realizations).
  * Lets a caller drop the affected realizations instead of the whole batch.  Synchronises. */
 tnmc_status tnmc_realization_status(tnmc_ctx* ctx, int32_t* out_host);
+
+/* The same per-realization failure flags without synchronising: queues on the context's stream
+ * a copy of the n_real status words into out_dev (device, n_real uint32): 0 = no failure, bit 0
+ * set = a numeric failure as above (bit 1: a bounded wait ran out).  Lets a caller that reuses a
+ * context for successive batches keep each batch's flags.  Errors: TNMC_ERR_ARG, TNMC_ERR_CUDA. */
+tnmc_status tnmc_realization_status_async(tnmc_ctx* ctx, uint32_t* out_dev);
 
 /* Kernel launch accounting: number of kernels this context launched since creation. */
 int64_t tnmc_launch_count(const tnmc_ctx* ctx);
@@ -270,7 +332,7 @@ size_t tnmc_estimate_device_bytes(int L, int n_real, int chi, const tnmc_opts* o
  *
  * The paper runs its disorder realizations as fixed sets (Sec. III); each realization is an
  * independent problem: couplings (Sec. III.A), environments (Sec. II.B), proposals with
- * log q (Sec. II.C), Metropolis and observables (Sec. III.C).  The server takes such
+ * log q (Sec. II.B), Metropolis and observables (Sec. III.C).  The server takes such
  * problems one request at a time from any thread, groups requests of equal (L, chi) into
  * batches of up to max_batch, runs up to max_inflight batches at once (one pooled context and
  * CUDA stream each) and returns per-request results as they finish.  A native scheduler

@@ -43,6 +43,9 @@ SIGNATURES = {
     "tnmc_selftest_bounded_wait": (c_int, [c_int, c_int64_p]),
     "tnmc_env_build_occupancy": (c_int, [c_int, c_int, c_int, c_int32_p, c_int32_p]),
     "tnmc_realization_status": (c_int, [c_void_p, c_int32_p]),
+    "tnmc_realization_status_async": (c_int, [c_void_p, c_void_p]),
+    "tnmc_disorder_average": (c_int, [c_void_p, c_int, c_int, c_double, c_void_p]),
+    "tnmc_nishimori_beta": (c_int, [c_double, c_double_p]),
     "tnmc_estimate_device_bytes": (c_size_t, [c_int, c_int, c_int, c_void_p, c_int]),
     "tnmc_server_create": (c_int, [c_void_p, ctypes.POINTER(c_void_p)]),
     "tnmc_server_submit": (c_int, [c_void_p, c_void_p, c_int64_p]),
@@ -56,8 +59,13 @@ SIGNATURES = {
 }
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
+
+
 class Opts(ctypes.Structure):
-    _fields_ = [("precision", c_int), ("n_chains", c_int), ("n_therm", c_int), ("stream", c_void_p)]
+    _fields_ = [("precision", c_int), ("n_chains", c_int), ("n_therm", c_int), ("stream", c_void_p),
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", c_void_p)]
 
 
 class Obs(ctypes.Structure):
@@ -65,7 +73,20 @@ class Obs(ctypes.Structure):
                 ("clamps", c_int64), ("E", c_double), ("E2", c_double), ("m_abs", c_double),
                 ("m2", c_double), ("m4", c_double), ("q", c_double), ("q_abs", c_double),
                 ("q2", c_double), ("q4", c_double), ("m_edge", c_double), ("m_edge_abs", c_double),
-                ("m_edge2", c_double)]
+                ("m_edge2", c_double), ("n_tests", c_int64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+# order of the mean / se arrays of tnmc_disorder
+DIS_KEYS = ["E", "E2", "m_abs", "m2", "m4", "q", "q_abs", "q2", "q4", "m_edge", "m_edge_abs", "m_edge2"]
+
+
+class Disorder(ctypes.Structure):
+    _fields_ = [("n_used", ctypes.c_int32), ("n_dropped", ctypes.c_int32),
+                ("mean", c_double * len(DIS_KEYS)), ("se", c_double * len(DIS_KEYS)),
+                ("U_m", c_double), ("Q_q", c_double), ("q2_sq", c_double), ("chi_q", c_double),
+                ("chi_edge", c_double), ("acceptance", c_double), ("n_prop", c_int64), ("n_tests", c_int64),
+                ("n_acc", c_int64), ("clamps", c_int64)]
 
 
 class ServerOpts(ctypes.Structure):

@@ -37,7 +37,7 @@ def run_one(L, chi, p, R, n, precision, seed0):
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     ok = [o for o, s in zip(obs, status) if s == 0]
-    rates = np.array([o["n_acc"] / max(1, o["n_prop"] - 2) for o in ok])
+    rates = np.array([o["n_acc"] / max(1, o["n_tests"]) for o in ok])
     pa = float(rates.mean()) if len(rates) else float("nan")
     se = float(rates.std(ddof=1) / math.sqrt(len(rates))) if len(rates) > 1 else 0.0
     return dict(L=L, chi=chi, p=p, T=1.0 / beta, R=R, proposals_per_chain=n, precision=precision,

@@ -69,6 +69,10 @@ struct tnmc_ctx {
   // device buffers come from the stream-ordered allocator where the device has one, so that
   // freeing a context never waits for work on other streams (cudaFree synchronises the device)
   bool async_alloc = false;
+  // the caller's allocator (tnmc_opts.alloc / free), when given
+  tnmc_alloc_fn user_alloc = nullptr;
+  tnmc_free_fn user_free = nullptr;
+  void* alloc_user = nullptr;
   // pinned staging ring for the small per-batch host inputs (inverse temperatures, seeds),
   // so that host-to-device copies are truly asynchronous and the caller's buffers can be
   // reused at once; a slot is reused only after its copy has executed
@@ -96,11 +100,16 @@ template <typename P>
 tnmc_status dalloc(tnmc_ctx* c, P** p, size_t bytes) {
   void* q = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = c->async_alloc ? cudaMallocAsync(&q, bytes, c->stream) : cudaMalloc(&q, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(c, TNMC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
-                                     cudaGetErrorString(e));
+  if (c->user_alloc) {
+    q = c->user_alloc(bytes, reinterpret_cast<void*>(c->stream), c->alloc_user);
+    if (!q) return fail(c, TNMC_ERR_OOM, "the caller's allocator returned NULL for " + std::to_string(bytes) + " bytes");
+  } else {
+    cudaError_t e = c->async_alloc ? cudaMallocAsync(&q, bytes, c->stream) : cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, TNMC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                       cudaGetErrorString(e));
+    }
   }
   c->allocs.push_back(q);
   c->alloc_sizes.push_back(bytes);
@@ -108,15 +117,24 @@ tnmc_status dalloc(tnmc_ctx* c, P** p, size_t bytes) {
   return TNMC_OK;
 }
 
+// Return one block to whoever allocated it, in stream order on st.
+void release_block(tnmc_ctx* c, void* p, size_t bytes, cudaStream_t st) {
+  if (c->user_free) c->user_free(p, bytes, reinterpret_cast<void*>(st), c->alloc_user);
+  else if (c->async_alloc) cudaFreeAsync(p, st);
+  else cudaFree(p);
+}
+
 void dfree(tnmc_ctx* c, void* p) {
   if (!p) return;
+  size_t bytes = 0;
   for (size_t i = 0; i < c->allocs.size(); ++i)
     if (c->allocs[i] == p) {
+      bytes = c->alloc_sizes[i];
       c->allocs.erase(c->allocs.begin() + i);
       c->alloc_sizes.erase(c->alloc_sizes.begin() + i);
       break;
     }
-  if (c->async_alloc) cudaFreeAsync(p, c->stream); else cudaFree(p);
+  release_block(c, p, bytes, c->stream);
 }
 
 int round_chi(int chi) {
@@ -246,6 +264,8 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
     return fail(nullptr, TNMC_ERR_UNSUPPORTED, "the FP64 path is built for chi <= 32 (chi = 64 needs 256 KB of shared memory)");
   if (opts->precision < 0 || opts->precision > 3) return fail(nullptr, TNMC_ERR_ARG, "unknown precision");
   if (opts->n_chains < 1 || opts->n_chains > 8) return fail(nullptr, TNMC_ERR_ARG, "n_chains must be in [1, 8]");
+  if ((opts->alloc == nullptr) != (opts->free == nullptr))
+    return fail(nullptr, TNMC_ERR_ARG, "opts.alloc and opts.free must be given together");
   for (int k = 0; k < n_real; ++k)
     if (!(beta_host[k] > 0.0) || !std::isfinite(beta_host[k]))
       return fail(nullptr, TNMC_ERR_ARG, "beta must be positive and finite");
@@ -268,6 +288,7 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
   int pools = 0;
   if (cudaDeviceGetAttribute(&pools, cudaDevAttrMemoryPoolsSupported, c->device) != cudaSuccess) cudaGetLastError();
   c->async_alloc = pools != 0;
+  c->user_alloc = opts->alloc; c->user_free = opts->free; c->alloc_user = opts->alloc_user;
   c->t_size = c->precision == TNMC_FP64 ? 8 : 4;
   c->te_size = c->precision == TNMC_FP64 ? 8 : (c->precision == TNMC_MIXED_BF16 ? 2 : 4);
   const int CHI = c->CHI;
@@ -488,14 +509,12 @@ tnmc_status tnmc_eval_conditionals(tnmc_ctx* c, int n, const int8_t* spins_dev, 
   double* lq = logq_dev;
   double* tmp = nullptr;
   if (!lq) {
-    if (cudaMalloc(&tmp, sizeof(double) * (size_t)c->n_real * n) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(c, TNMC_ERR_OOM, "log q buffer");
-    }
+    tnmc_status sa = dalloc(c, &tmp, sizeof(double) * (size_t)c->n_real * n);
+    if (sa) return sa;
     lq = tmp;
   }
   tnmc_status s = run_sample(c, n, 0, spins_dev, lq, qplus_dev, false);
-  if (tmp) { cudaStreamSynchronize(c->stream); cudaFree(tmp); }
+  if (tmp) dfree(c, tmp);       // stream-ordered: the sweep that writes it runs first
   return s;
 }
 
@@ -544,7 +563,13 @@ tnmc_status tnmc_observables(tnmc_ctx* c, tnmc_obs* out_host) {
   cudaError_t e = cudaMemcpy(acc.data(), c->acc, acc.size() * sizeof(double), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemcpy(cl.data(), c->clamps, cl.size() * sizeof(int64_t), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "observables copy");
-  for (int k = 0; k < c->n_real; ++k) tnmc::obs_from_acc(&acc[(size_t)k * tnmc::ACC_SLOTS], cl[k], &out_host[k]);
+  std::vector<unsigned> rst(c->n_real);
+  e = cudaMemcpy(rst.data(), c->rstatus, sizeof(unsigned) * rst.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status copy");
+  for (int k = 0; k < c->n_real; ++k) {
+    tnmc::obs_from_acc(&acc[(size_t)k * tnmc::ACC_SLOTS], cl[k], &out_host[k]);
+    out_host[k].status = (rst[k] & tnmc::ST_NUMERIC) ? TNMC_ERR_NUMERIC : TNMC_OK;
+  }
   // every realization is filled in; a numeric failure of some is reported after the fact
   return check_status(c);
 }
@@ -553,6 +578,7 @@ tnmc_status tnmc_reset_chains(tnmc_ctx* c) {
   if (!c) return fail(nullptr, TNMC_ERR_ARG, "NULL context");
   const size_t chains = (size_t)c->n_real * c->n_chains;
   cudaError_t e = cudaMemsetAsync(c->have_state, 0, sizeof(int) * chains, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->rstatus, 0, sizeof(unsigned) * c->n_real, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->acc, 0, sizeof(double) * (size_t)c->n_real * tnmc::ACC_SLOTS, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->clamps, 0, sizeof(int64_t) * c->n_real, c->stream);
@@ -564,9 +590,7 @@ tnmc_status tnmc_reset_chains(tnmc_ctx* c) {
 tnmc_status tnmc_destroy(tnmc_ctx* c) {
   if (!c) return TNMC_OK;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
-  for (void* p : c->allocs) {
-    if (c->async_alloc) cudaFreeAsync(p, c->stream); else cudaFree(p);
-  }
+  for (size_t i = 0; i < c->allocs.size(); ++i) release_block(c, c->allocs[i], c->alloc_sizes[i], c->stream);
   if (c->h_stage) {
     tnmc::pinned_put(c->h_stage, (size_t)32 * c->cap * tnmc_ctx::kStageSlots);
     for (int s = 0; s < tnmc_ctx::kStageSlots; ++s) if (c->stage_ev[s]) cudaEventDestroy(c->stage_ev[s]);
@@ -582,10 +606,9 @@ size_t tnmc_env_bytes(const tnmc_ctx* c) { return c ? c->env_bytes : 0; }
 tnmc_status tnmc_build_stats(tnmc_ctx* c, int64_t* out_host) {
   if (!c || !out_host) return fail(c, TNMC_ERR_ARG, "NULL argument");
   if (!c->env_built) return fail(c, TNMC_ERR_STATE, "no environments");
-  tnmc_status s = check_status(c);
-  if (s) return s;
   std::vector<long long> st((size_t)4 * c->n_real);
-  cudaError_t e = cudaMemcpy(st.data(), c->stats, st.size() * sizeof(long long), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpyAsync(st.data(), c->stats, st.size() * sizeof(long long), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stats copy");
   int64_t mx = 0, unc = 0, tot = 0, nsvd = 0;
   for (int k = 0; k < c->n_real; ++k) {
@@ -604,6 +627,13 @@ tnmc_status tnmc_realization_status(tnmc_ctx* c, int32_t* out_host) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "status copy");
   for (int k = 0; k < c->n_real; ++k) out_host[k] = (st[k] & tnmc::ST_NUMERIC) ? TNMC_ERR_NUMERIC : TNMC_OK;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_realization_status_async(tnmc_ctx* c, uint32_t* out_dev) {
+  if (!c || !out_dev) return fail(c, TNMC_ERR_ARG, "NULL argument");
+  cudaError_t e = cudaMemcpyAsync(out_dev, c->rstatus, sizeof(unsigned) * c->n_real, cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status copy");
   return TNMC_OK;
 }
 
@@ -750,6 +780,8 @@ void obs_from_acc(const double* a, int64_t clamps, tnmc_obs* out) {
   o.m2 = a[ACC_M2] / nm; o.m4 = a[ACC_M4] / nm;
   o.q = a[ACC_Q] / nq; o.q_abs = a[ACC_QABS] / nq; o.q2 = a[ACC_Q2] / nq; o.q4 = a[ACC_Q4] / nq;
   o.m_edge = a[ACC_MEDGE] / nm; o.m_edge_abs = a[ACC_MEDGEABS] / nm; o.m_edge2 = a[ACC_MEDGE2] / nm;
+  o.n_tests = (int64_t)llround(a[ACC_NTEST]);
+  o.status = TNMC_OK;
 }
 
 // A new batch on a pooled context (used by the request server): n_active <= capacity
@@ -802,9 +834,7 @@ void ctx_set_stream(tnmc_ctx* c, cudaStream_t st) { c->stream = st; }
 
 void ctx_release(tnmc_ctx* c, cudaStream_t st) {
   if (!c) return;
-  for (void* p : c->allocs) {
-    if (c->async_alloc) cudaFreeAsync(p, st); else cudaFree(p);
-  }
+  for (size_t i = 0; i < c->allocs.size(); ++i) release_block(c, c->allocs[i], c->alloc_sizes[i], st);
   if (c->h_stage) {
     tnmc::pinned_put(c->h_stage, (size_t)32 * c->cap * tnmc_ctx::kStageSlots);
     for (int k = 0; k < tnmc_ctx::kStageSlots; ++k) if (c->stage_ev[k]) cudaEventDestroy(c->stage_ev[k]);

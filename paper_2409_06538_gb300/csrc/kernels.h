@@ -104,7 +104,9 @@ cudaError_t launch_unpack(const uint32_t* packed, int words, int N, int64_t n_cf
 // accumulator slots in AcceptArgs::acc
 enum AccSlot {
   ACC_NPROP = 0, ACC_NACC, ACC_NMEAS, ACC_NMEASQ, ACC_E, ACC_E2, ACC_MABS, ACC_M2, ACC_M4,
-  ACC_Q, ACC_QABS, ACC_Q2, ACC_Q4, ACC_MEDGE, ACC_MEDGEABS, ACC_MEDGE2, ACC_SLOTS = 16
+  ACC_Q, ACC_QABS, ACC_Q2, ACC_Q4, ACC_MEDGE, ACC_MEDGEABS, ACC_MEDGE2,
+  ACC_NTEST,            // Metropolis tests: proposals after each chain's initial state
+  ACC_SLOTS = 17
 };
 
 }  // namespace tnmc

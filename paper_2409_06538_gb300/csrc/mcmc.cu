@@ -62,6 +62,7 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
   const int N = a.L * a.L;
   __shared__ double red[32];
   __shared__ double nacc_s[8];
+  __shared__ double ntest_s[8];
   int* cur = a.cur_idx + (size_t)real * nc * n;
   // proposals of this call that the realization uses: all n, or what is left of its own
   // per-realization total after step0 (the rest is skipped as if never drawn)
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
     double cE = have ? (double)a.cur_energy[sidx] : 0.0;
     double cq = have ? a.cur_logq[sidx] : 0.0;
     int c = -1;
-    int64_t nacc = 0;
+    int64_t nacc = 0, ntest = 0;
     for (int k = 0; k < n; ++k) {
       if (k >= lim) {                       // beyond this realization's own proposal count
         if (a.accepted) a.accepted[base + k] = 0;
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
         const double delta = (-beta * E - lq) - (-beta * cE - cq);
         const double u = uniform(seed, 0u, (uint32_t)(a.step0 + k), (uint32_t)ch, PURPOSE_ACCEPT);
         ok = (delta >= 0.0) || (u < exp(delta));
+        ++ntest;
         if (ok) ++nacc;
       }
       if (ok) { have = true; cE = E; cq = lq; c = k; }
@@ -101,6 +103,7 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
       cur[(size_t)ch * n + k] = c;
     }
     nacc_s[ch] = (double)nacc;
+    ntest_s[ch] = (double)ntest;
   }
   __syncthreads();
 
@@ -147,10 +150,11 @@ __global__ void __launch_bounds__(kAcceptThreads) accept_kernel(AcceptArgs a) {
   sEd = block_sum(sEd, red); sEda = block_sum(sEda, red); sEd2 = block_sum(sEd2, red);
   if (tid == 0) {
     double* acc = a.acc + (size_t)real * ACC_SLOTS;
-    double na = 0;
-    for (int ch = 0; ch < nc && ch < 8; ++ch) na += nacc_s[ch];
+    double na = 0, nt = 0;
+    for (int ch = 0; ch < nc && ch < 8; ++ch) { na += nacc_s[ch]; nt += ntest_s[ch]; }
     acc[ACC_NPROP] += (double)nc * lim;
     acc[ACC_NACC] += na;
+    acc[ACC_NTEST] += nt;
     acc[ACC_NMEAS] += nm;
     acc[ACC_NMEASQ] += nq;
     acc[ACC_E] += sE; acc[ACC_E2] += sE2; acc[ACC_MABS] += sMa; acc[ACC_M2] += sM2; acc[ACC_M4] += sM4;

@@ -26,10 +26,12 @@ std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // The status code is the whole error report of this entry point; the text is kept for a
-// debugger only.
+// debugger only (written under g_err_mu, since calls may come from several threads).
+std::mutex g_err_mu;
 std::string g_err;
 
 tnmc_status err(tnmc_status s, const std::string& m) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
   g_err = m;
   return s;
 }
@@ -75,7 +77,9 @@ tnmc_status run(int L, int n_real, int chi, int CHI, const int8_t* J, const doub
   if (off > kNoAllocScratchBytes)
     return err(TNMC_ERR_ARG, "tnmc_build_env_noalloc: needs " + std::to_string(off) + " bytes of scratch, the limit is " +
                                  std::to_string(kNoAllocScratchBytes) + " (reduce n_real, L or chi)");
-  // the status word must start at zero; every other scratch word is written before it is read
+  // the build kernel writes no status (it has no failure to report), but the word is cleared
+  // so that the scratch a call leaves behind never carries another call's bits; every other
+  // scratch word is written before it is read
   cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return err(TNMC_ERR_CUDA, std::string("status reset: ") + cudaGetErrorString(e));
   tnmc::EnvBuildArgs<T, TE> a{L, n_real, chi, J, beta, static_cast<TE*>(env), kdim, dqr, lam, logz, rowbuf, Rstore,

@@ -177,7 +177,11 @@ sample_kernel(SampleArgs a) {
             set_status(a.status, ST_NUMERIC);
             if (a.real_status) set_status(a.real_status + real, ST_NUMERIC);
           }
-          s = 1; lqs = T(-0.6931471805599453);
+          // the realization is flagged; the spin is still drawn from the q = 1/2 it logs,
+          // so that log q stays the probability the proposal was drawn with
+          if (forced) s = forced[(size_t)r * L + c];
+          else s = (philox_m53(seed, (uint32_t)(r * L + c), step, (uint32_t)chain) < (1ull << 52)) ? 1 : -1;
+          lqs = T(-0.6931471805599453);
         } else {
           qp = w0 / tot;
           const T qm = w1 / tot;
@@ -389,7 +393,11 @@ sample_kernel_wide(SampleArgs a) {
             set_status(a.status, ST_NUMERIC);
             if (a.real_status) set_status(a.real_status + real, ST_NUMERIC);
           }
-          s = 1; lqs = T(-0.6931471805599453);
+          // the realization is flagged; the spin is still drawn from the q = 1/2 it logs,
+          // so that log q stays the probability the proposal was drawn with
+          if (forced) s = forced[(size_t)r * L + c];
+          else s = (philox_m53(seed, (uint32_t)(r * L + c), step, (uint32_t)chain) < (1ull << 52)) ? 1 : -1;
+          lqs = T(-0.6931471805599453);
         } else {
           qp = w0 / tot;
           const T qm = w1 / tot;

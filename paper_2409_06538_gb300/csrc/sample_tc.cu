@@ -377,7 +377,16 @@ __global__ void __launch_bounds__(128) sample_tc_kernel(SampleArgs a) {
             set_status(a.status, ST_NUMERIC);
             if (a.real_status) set_status(a.real_status + real, ST_NUMERIC);
           }
-          s = 1; lqs = -0.6931471805599453f;
+          // the realization is flagged; the spin is still drawn from the q = 1/2 it logs,
+          // so that log q stays the probability the proposal was drawn with
+          if (forced) {
+            s = forced[(size_t)r * L + c];
+          } else {
+            const Philox4 o = philox4x32_10((uint32_t)(r * L + c), step, (uint32_t)chain, PURPOSE_SPIN,
+                                            (uint32_t)seed, (uint32_t)(seed >> 32));
+            s = ((o.x0 >> 5) < (1u << 26)) ? 1 : -1;      // m53 < 2^52
+          }
+          lqs = -0.6931471805599453f;
         } else {
           qp = w0 / tot;
           const float qm = w1 / tot;

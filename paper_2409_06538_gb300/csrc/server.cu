@@ -209,6 +209,7 @@ void finish_request(tnmc_server* s, const Pending& q, tnmc_status st, int batch_
   r.t_submit = q.t_submit;
   r.t_start = t_start;
   r.t_done = s->now();
+  r.obs.status = st;
   if (p && st == TNMC_OK) {
     tnmc::obs_from_acc(p->acc_h + (size_t)k * tnmc::ACC_SLOTS, p->clamps_h[k], &r.obs);
     r.log_z = p->logz_h[k];

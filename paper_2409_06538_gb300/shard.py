@@ -16,10 +16,10 @@ def shard_seeds(seeds, rank, world):
     return seeds[start:start + base + (1 if rank < extra else 0)]
 
 
-def gather_disorder_average(per_realization, group=None, L=None, beta=None):
+def gather_disorder_average(per_realization, L, beta, group=None):
     """All-gather the per-realization observable dicts of every rank (torch.distributed,
     any backend) and return the disorder average over all realizations on every rank
-    (with the susceptibilities when L and beta are given)."""
+    (tnmc_disorder_average, for lattice side L at inverse temperature beta)."""
     import torch.distributed as dist
     world = dist.get_world_size(group)
     parts = [None] * world

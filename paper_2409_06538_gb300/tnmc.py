@@ -1,7 +1,6 @@
 """Python binding of the TNMC C ABI.  PyTorch provides device buffers and the CUDA stream;
 all arithmetic of the method runs in libtnmc.so."""
 import ctypes
-import math
 
 import numpy as np
 import torch
@@ -21,9 +20,31 @@ def _stream_handle(stream):
     return _c.c_void_p(stream.cuda_stream)
 
 
+class _TorchAllocator:
+    """Device memory for a context from PyTorch's caching allocator (tnmc_opts.alloc / free):
+    stream-ordered blocks on the context's stream, returned to PyTorch's cache on release."""
+
+    def __init__(self, device):
+        self.device = int(device)
+
+        def alloc(nbytes, stream, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device, stream=int(stream or 0))
+            except Exception:          # out of memory: the library reports TNMC_ERR_OOM
+                return None
+
+        def free(ptr, nbytes, stream, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = _capi.ALLOC_FN(alloc)
+        self.free = _capi.FREE_FN(free)
+
+
 def nishimori_beta(p):
-    """Inverse temperature on the Nishimori line exp(-2/T) = p/(1-p), |J| = 1."""
-    return 0.5 * math.log((1.0 - p) / p)
+    """Inverse temperature on the Nishimori line, exp(-2/T) = p/(1-p) (tnmc_nishimori_beta)."""
+    out = _c.c_double(0.0)
+    _capi.check(_capi.load().tnmc_nishimori_beta(float(p), _c.byref(out)))
+    return out.value
 
 
 def env_build_occupancy(L, chi, precision="tf32"):
@@ -48,7 +69,10 @@ def couplings_pmj(L, seeds, p, stream=None):
 class TNMC:
     """n_real realizations of one (L, chi) bucket behind one library context."""
 
-    def __init__(self, L, couplings, beta, seeds, chi, precision="fp64", n_chains=2, n_therm=0, stream=None):
+    def __init__(self, L, couplings, beta, seeds, chi, precision="fp64", n_chains=2, n_therm=0, stream=None,
+                 allocator="torch"):
+        """allocator: "torch" -- device buffers come from PyTorch's caching allocator through the
+        library's allocator hooks; "library" -- the library allocates them itself."""
         self.lib = _capi.load()
         self.L, self.chi, self.n_chains = int(L), int(chi), int(n_chains)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -64,6 +88,12 @@ class TNMC:
         self._keep = (J, beta, seeds)
         opts = _capi.Opts(_capi.PRECISIONS[precision], self.n_chains, int(n_therm),
                           _stream_handle(self.stream))
+        if allocator == "torch":
+            # kept alive with the context: the library calls it until tnmc_destroy
+            self._alloc = _TorchAllocator(torch.cuda.current_device())
+            opts.alloc, opts.free = self._alloc.alloc, self._alloc.free
+        elif allocator != "library":
+            raise ValueError(f"unknown allocator {allocator!r}")
         ctx = _c.c_void_p()
         code = self.lib.tnmc_create(self.L, self.n_real, jp, beta.ctypes.data_as(_capi.c_double_p),
                                     seeds.ctypes.data_as(_capi.c_uint64_p), self.chi, _c.byref(opts),
@@ -174,6 +204,12 @@ class TNMC:
         self._chk(self.lib.tnmc_realization_status(self.ctx, out.ctypes.data_as(_capi.c_int32_p)))
         return out
 
+    def realization_status_async(self, out):
+        """Queue a copy of the per-realization status words into `out` (int32 cuda tensor of
+        n_real; 0 = no failure) on this context's stream, without synchronising."""
+        assert out.is_cuda and out.dtype == torch.int32 and out.numel() >= self.n_real
+        self._chk(self.lib.tnmc_realization_status_async(self.ctx, _ptr(out)))
+
     def device_bytes(self):
         return int(self.lib.tnmc_device_bytes(self.ctx))
 
@@ -195,26 +231,23 @@ class TNMC:
             pass
 
 
-def disorder_average(obs, L=None, beta=None):
-    """Disorder means [.] and standard errors over per-realization thermal means, with the
-    Binder ratios U_m = [<m^4>]/[<m^2>]^2 and Q_q = [<q^4>]/[<q^2>]^2, and given L (and beta)
-    the susceptibilities chi_q = (L^2/T)([<q^2>] - [<q>]^2) and chi_edge = L [<m_edge^2>]
-    (Sec. III.C, Eq. eq:susEA)."""
-    keys = ["E", "E2", "m_abs", "m2", "m4", "q", "q_abs", "q2", "q4", "m_edge", "m_edge_abs", "m_edge2"]
-    keys = [k for k in keys if k in obs[0]]
-    R = len(obs)
-    out = {}
-    for k in keys:
-        x = np.array([o[k] for o in obs])
-        out[k] = (float(x.mean()), float(x.std(ddof=1) / math.sqrt(R)) if R > 1 else 0.0)
-    out["U_m"] = out["m4"][0] / out["m2"][0] ** 2 if out["m2"][0] > 0 else float("nan")
-    out["Q_q"] = out["q4"][0] / out["q2"][0] ** 2 if out["q2"][0] > 0 else float("nan")
-    nacc = sum(o["n_acc"] for o in obs)
-    nprop = sum(o["n_prop"] for o in obs)
-    out["acceptance"] = nacc / max(1, nprop)
-    out["clamps"] = int(sum(o["clamps"] for o in obs))
-    if L is not None and beta is not None:
-        out["chi_q"] = L * L * beta * (out["q2"][0] - out["q"][0] ** 2)
-    if L is not None and "m_edge2" in out:
-        out["chi_edge"] = L * out["m_edge2"][0]
+def disorder_average(obs, L, beta):
+    """Disorder averages of per-realization thermal means (tnmc_disorder_average): for each
+    quantity (mean, standard error), the Binder ratios U_m and Q_q, [<q^2>^2], the
+    susceptibilities chi_q and chi_edge and the acceptance rate, over the realizations whose
+    status is 0 (n_used; n_dropped were flagged).  obs: dicts as TNMC.observables() returns."""
+    lib = _capi.load()
+    arr = (_capi.Obs * len(obs))()
+    for o, d in zip(arr, obs):
+        for k, _ in _capi.Obs._fields_:
+            if k in d:
+                setattr(o, k, d[k])
+    res = _capi.Disorder()
+    code = lib.tnmc_disorder_average(arr, len(obs), int(L), float(beta), _c.byref(res))
+    if code not in (0, 4):
+        _capi.check(code)
+    out = {k: (res.mean[i], res.se[i]) for i, k in enumerate(_capi.DIS_KEYS)}
+    for k in ("U_m", "Q_q", "q2_sq", "chi_q", "chi_edge", "acceptance", "n_used", "n_dropped", "n_prop",
+              "n_tests", "n_acc", "clamps"):
+        out[k] = getattr(res, k)
     return out

@@ -212,7 +212,9 @@ def test_metropolis_and_observables_parity(tn):
         for key in ("E", "E2", "m_abs", "m2", "m4", "q", "q_abs", "q2", "q4", "m_edge", "m_edge_abs", "m_edge2"):
             assert abs(obs[k][key] - ref[key]) <= 1e-12 * max(1.0, abs(ref[key])), key
         assert obs[k]["n_prop"] == 2 * 2 * n
+        assert obs[k]["n_tests"] == 2 * 2 * n - 2          # each chain's initial state is no test
         assert obs[k]["n_acc"] == int(fl[k].sum()) - 2
+        assert obs[k]["status"] == 0
         per.append(ref)
     assert 0.0 < np.mean([o["n_acc"] for o in obs]) < 2 * 2 * n
     assert np.all(ctx.realization_status() == 0)
@@ -230,7 +232,8 @@ def test_observables_match_independent_oracle_run(tn):
     ctx.build_env(return_logz=False)
     ctx.propose(n, 0)
     ctx.accept()
-    g = pkg.disorder_average(ctx.observables())
+    gobs = ctx.observables()
+    g = pkg.disorder_average(gobs, L, beta)
     per = []
     for s in seeds:
         env = oracle_envs(s, L, p, chi)
@@ -244,7 +247,17 @@ def test_observables_match_independent_oracle_run(tn):
     for key in ("E", "m2", "q2", "m_edge2"):
         se = np.hypot(g[key][1], o[key][1])
         assert abs(g[key][0] - o[key][0]) <= 2 * se + 1e-12, key
-    assert abs(g["U_m"] - o["U_m"]) < 0.05
+
+    def jackknife_se(m4, m2):
+        # standard error of the ratio of means [m4]/[m2]^2 by leave-one-out over realizations
+        m4, m2 = np.asarray(m4), np.asarray(m2)
+        R = len(m4)
+        loo = np.array([np.delete(m4, i).mean() / np.delete(m2, i).mean() ** 2 for i in range(R)])
+        return np.sqrt((R - 1) / R * ((loo - loo.mean()) ** 2).sum())
+
+    se_g = jackknife_se([x["m4"] for x in gobs], [x["m2"] for x in gobs])
+    se_o = jackknife_se([x["m4"] for x in per], [x["m2"] for x in per])
+    assert abs(g["U_m"] - o["U_m"]) <= 2 * np.hypot(se_g, se_o), (g["U_m"], o["U_m"], se_g, se_o)
 
 
 def test_set_realizations_reuses_a_context(tn):

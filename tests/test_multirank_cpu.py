@@ -1,6 +1,7 @@
 """The multi-rank path on CPU (gloo, world size 2): realizations are sharded with no
-data-path exchange, and the one gather at the end reproduces the single-process disorder
-averages exactly."""
+data-path exchange, and the one gather at the end -- through the library's host-side
+tnmc_disorder_average -- reproduces the single-process disorder averages exactly, on
+per-realization thermal means that the oracle's own TNMC run produced."""
 import os
 import socket
 
@@ -18,13 +19,15 @@ def _free_port():
     return port
 
 
-def _fake_obs(seed):
-    """Per-realization thermal means standing in for one realization's run (host data only)."""
-    r = np.random.default_rng(int(seed))
-    keys = ["E", "E2", "m_abs", "m2", "m4", "q", "q_abs", "q2", "q4", "m_edge", "m_edge_abs", "m_edge2"]
-    d = {k: float(r.random()) for k in keys}
-    d.update(n_acc=int(r.integers(0, 100)), n_prop=100, clamps=0)
-    return d
+_OBS_CACHE = {}
+
+
+def _realization_obs(seed):
+    """Thermal means of one seeded realization (L = 4, chi = 2, p = 0.109) from the oracle."""
+    if seed not in _OBS_CACHE:
+        from tests.test_disorder_host import oracle_realizations
+        _OBS_CACHE[seed] = oracle_realizations(4, 0.109, 2, [int(seed)], 12, 2)[0]
+    return _OBS_CACHE[seed]
 
 
 def _worker(rank, world, port, seeds, out_path):
@@ -34,7 +37,7 @@ def _worker(rank, world, port, seeds, out_path):
     from paper_2409_06538_gb300 import shard
     dist.init_process_group("gloo", rank=rank, world_size=world)
     mine = shard.shard_seeds(seeds, rank, world)
-    avg, n = shard.gather_disorder_average([_fake_obs(s) for s in mine], L=16, beta=0.9)
+    avg, n = shard.gather_disorder_average([_realization_obs(s) for s in mine], 4, 0.9)
     if rank == 0:
         np.save(out_path, np.array([avg["E"][0], avg["E"][1], avg["m2"][0], avg["U_m"], avg["Q_q"],
                                     avg["acceptance"], n, avg["chi_q"], avg["chi_edge"]], dtype=np.float64))
@@ -53,12 +56,13 @@ def test_shards_are_disjoint_and_cover():
 
 def test_gloo_two_ranks_reproduce_single_process(tmp_path):
     import torch.multiprocessing as mp
-    from paper_2409_06538_gb300 import disorder_average
-    seeds = np.arange(100, 137)
+    from paper_2409_06538_gb300 import build, disorder_average
+    build()
+    seeds = np.arange(100, 113)
     out = str(tmp_path / "avg.npy")
     mp.spawn(_worker, args=(2, _free_port(), seeds, out), nprocs=2, join=True)
     got = np.load(out)
-    ref = disorder_average([_fake_obs(s) for s in seeds], 16, 0.9)
+    ref = disorder_average([_realization_obs(s) for s in seeds], 4, 0.9)
     want = np.array([ref["E"][0], ref["E"][1], ref["m2"][0], ref["U_m"], ref["Q_q"], ref["acceptance"], len(seeds),
                      ref["chi_q"], ref["chi_edge"]])
     assert np.allclose(got, want, rtol=0, atol=1e-12)

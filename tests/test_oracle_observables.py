@@ -77,3 +77,48 @@ def test_susceptibility_invariants():
     out = metropolis.disorder_average(sym, L, beta)
     assert abs(out["chi_q"] - L * L * beta * np.mean([d["q2"] for d in sym])) < 1e-12
     assert abs(out["chi_edge"] - L * 0.04) < 1e-15
+
+
+def _enumerated_realization(L, same_states):
+    """Per-step observables over every ordered pair (s, s') of an L x L lattice's states, each
+    pair once: chain 0 takes s, chain 1 takes s' (independent uniform replicas, i.e. infinite
+    temperature) -- or, with same_states, chain 1 repeats chain 0 (overlap q = 1 at every step)."""
+    S = brute.all_states(L, L)
+    n = len(S)
+    i0 = np.repeat(np.arange(n), n)
+    i1 = np.tile(np.arange(n), n)
+    if same_states:
+        i0 = i1 = np.arange(n)
+    cur = np.stack([S[i0], S[i1]])
+    return metropolis.thermal_means(metropolis.chain_observables(cur, np.zeros(cur.shape[:2])), 0)
+
+
+def test_binder_ratios_closed_forms():
+    """Eq. eq:binderEA as ratios of disorder means, pinned by closed forms.  N independent
+    uniform spins have <m^2> = 1/N and <m^4> = (3N^2 - 2N)/N^4 (the fourth moment of a sum of
+    N independent +-1 variables), and the overlap of two independent such replicas has the same
+    law.  Realization A is exactly that (every pair of states of a 2 x 2 lattice, N = 4);
+    realization B has chain 1 equal to chain 0, so q = 1 at every step while m keeps the
+    independent-spin moments; realization C is the fully ordered state (m = q = 1).  The
+    ratios of the disorder means differ from the means of per-realization ratios and from the
+    other replica's moments, so a per-realization ratio, a swapped q2/q4 or an m/q mix-up fails."""
+    L = 2
+    N = L * L
+    m2, m4 = 1.0 / N, (3.0 * N * N - 2.0 * N) / N ** 4
+    A = _enumerated_realization(L, same_states=False)
+    B = _enumerated_realization(L, same_states=True)
+    for key, want in (("m2", m2), ("m4", m4), ("q2", m2), ("q4", m4)):
+        assert abs(A[key] - want) < 1e-15, key
+    assert abs(B["m2"] - m2) < 1e-15 and abs(B["m4"] - m4) < 1e-15
+    assert abs(B["q2"] - 1.0) < 1e-15 and abs(B["q4"] - 1.0) < 1e-15
+    C = dict(A, m_abs=1.0, m2=1.0, m4=1.0, q=1.0, q_abs=1.0, q2=1.0, q4=1.0)
+    out = metropolis.disorder_average([A, B])
+    assert abs(out["U_m"] - m4 / m2 ** 2) < 1e-13                      # 3 - 2/N = 2.5
+    assert abs(out["U_m"] - (3.0 - 2.0 / N)) < 1e-13
+    Qq = ((m4 + 1.0) / 2) / ((m2 + 1.0) / 2) ** 2                      # 1.48
+    assert abs(out["Q_q"] - Qq) < 1e-13
+    assert abs(out["q2_sq"] - (m2 ** 2 + 1.0) / 2) < 1e-15
+    out = metropolis.disorder_average([A, C])
+    assert abs(out["U_m"] - ((m4 + 1.0) / 2) / ((m2 + 1.0) / 2) ** 2) < 1e-13
+    per_real = ((3.0 - 2.0 / N) + 1.0) / 2                              # the wrong reading: 1.75
+    assert abs(out["U_m"] - per_real) > 0.2

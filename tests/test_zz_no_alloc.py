@@ -18,7 +18,7 @@ torch = pytest.importorskip("torch")
 def _noalloc_build(lib, L, chi, precision, J, beta, stream):
     R = J.shape[0]
     C = 4 if chi <= 4 else 8 if chi <= 8 else 16 if chi <= 16 else 32
-    el = 8 if precision == 0 else 4
+    el = 8 if precision == 0 else (2 if precision == 2 else 4)
     env = torch.zeros(R * L * L * 2 * C * C * el, dtype=torch.uint8, device="cuda")
     kdim = torch.zeros((R, L, L + 1), dtype=torch.int32, device="cuda")
     lam = torch.zeros((R, L), dtype=torch.float64, device="cuda")
@@ -29,12 +29,17 @@ def _noalloc_build(lib, L, chi, precision, J, beta, stream):
                                       ctypes.c_void_p(stream.cuda_stream))
     assert code == 0
     stream.synchronize()
-    dt = np.float64 if precision == 0 else np.float32
-    tiles = env.cpu().numpy().view(dt).reshape(R, L, L, 2, C, C)
+    raw = env.cpu().numpy()
+    if precision == 2:      # bfloat16: the high half of a float32
+        tiles = (raw.view(np.uint16).astype(np.uint32) << 16).view(np.float32)
+    else:
+        tiles = raw.view(np.float64 if precision == 0 else np.float32)
+    tiles = tiles.reshape(R, L, L, 2, C, C)
     return tiles, kdim.cpu().numpy(), lam.cpu().numpy(), logz.cpu().numpy(), C
 
 
-@pytest.mark.parametrize("precision_name,precision,tol", [("fp64", 0, 1e-12), ("fp32", 1, 1e-5)])
+@pytest.mark.parametrize("precision_name,precision,tol", [("fp64", 0, 1e-12), ("fp32", 1, 1e-5), ("bf16", 2, 1e-5),
+                                                          ("tf32", 3, 1e-5)])
 def test_noalloc_matches_regular_build_twice(precision_name, precision, tol):
     import paper_2409_06538_gb300 as tn
     from paper_2409_06538_gb300 import _capi
