@@ -134,9 +134,9 @@ template <typename T, int CHI> struct JStride {
 
 template <typename T, int CHI>
 __host__ __device__ constexpr size_t env_smem_elems() {
-  // CHI = 64: only Y and V (D*DP each) and the Householder vectors (4D) stay in shared memory;
+  // CHI = 64: only Y and V (D*DP each) and the Householder vectors (three of 2D) stay in shared memory;
   // M lives in per-realization global scratch and R, the tile are read from global memory
-  if (CHI > 32) return (size_t)2 * (2 * CHI) * JStride<T, CHI>::DP + (size_t)4 * (2 * CHI);
+  if (CHI > 32) return (size_t)2 * (2 * CHI) * JStride<T, CHI>::DP + (size_t)6 * (2 * CHI);
   // backward: M, R (D*D each), Y, V (D*DP each) + tile (2*CHI*CHI); P (D*CHI) lives in the Y
   //           region and Q (2*CHI*CHI) in the V region between their uses
   // forward : X (2D*D, aliases M and Y) + R (D*D) + tile; the Householder vectors use V
@@ -187,13 +187,13 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
   T* Xs = sm;                 // 2D x D col-major
 
   __shared__ T Wc[8];               // W[x][a][b] at x*4 + a*2 + b
-  int8_t* jv_s = reinterpret_cast<int8_t*>(kBig ? Vc + D * DP + 4 * D : Bt + TILE);   // Jv[r][c], L entries
+  int8_t* jv_s = reinterpret_cast<int8_t*>(kBig ? Vc + D * DP + 6 * D : Bt + TILE);   // Jv[r][c], L entries
   int8_t* jh_s = jv_s + args.L;                                // Jh[r+1][c], L-1 entries
   const T eb = (T)exp(beta), ebm = (T)exp(-beta);             // exp(+-beta): every Boltzmann weight
-  // Householder vectors (double-buffered; the V region is idle in the forward sweep unless
+  // Householder vectors (three slots; the V region is idle in the forward sweep unless
   // the forward matrix X fills Y and V, as for kBig)
   T (*vbuf)[2 * D] = reinterpret_cast<T (*)[2 * D]>(kBig ? Vc + D * DP : Vc);
-  __shared__ T vcoef[2];
+  __shared__ T vcoef[3];
   __shared__ T red[32];
   __shared__ T sig[D];
   __shared__ int sel[CHI];
@@ -307,6 +307,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       // Each lane owns rows lane + 32 t (t < m/32) of a column; the reflector vector is
       // stored zero above its pivot row, so the updates run over all rows unconditionally.
       constexpr int RPL = m / 32 > 0 ? m / 32 : 1;     // rows per lane
+      constexpr int CPW = (D + NWARP - 1) / NWARP;      // columns a warp owns: k = warp + NWARP t
       auto house = [&](int j) {   // executed by the owning warp for column j
         T* col = Xs + (size_t)j * m;
         T xr[RPL];
@@ -320,13 +321,14 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
         ss = warp_sum(ss);
         const T x0 = col[j];
         __syncwarp();                 // every lane has read the pivot before any lane writes
+        T* vj = vbuf[j % 3];
         if (ss <= tiny) {
 #pragma unroll
           for (int t = 0; t < RPL; ++t) {
             const int i = lane + 32 * t;
-            if (i < m) { vbuf[j & 1][i] = T(0); if (i > j) col[i] = T(0); }
+            if (i < m) { vj[i] = T(0); if (i > j) col[i] = T(0); }
           }
-          if (lane == 0) vcoef[j & 1] = T(0);
+          if (lane == 0) vcoef[j % 3] = T(0);
         } else {
           const T nrm = num<T>::sqrt_(ss);
           const T alpha = x0 >= T(0) ? -nrm : nrm;
@@ -335,48 +337,86 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
           for (int t = 0; t < RPL; ++t) {
             const int i = lane + 32 * t;
             if (i < m) {
-              vbuf[j & 1][i] = (i == j) ? v0 : xr[t];
+              vj[i] = (i == j) ? v0 : xr[t];
               if (i >= j) col[i] = (i == j) ? alpha : T(0);
             }
           }
-          if (lane == 0) vcoef[j & 1] = T(1) / (nrm * (nrm + (x0 >= T(0) ? x0 : -x0)));  // 2/|v|^2
+          if (lane == 0) vcoef[j % 3] = T(1) / (nrm * (nrm + (x0 >= T(0) ? x0 : -x0)));  // 2/|v|^2
         }
       };
+      // reflector jj applied to one column k (the pivot owner's next column)
+      auto apply1 = [&](int jj, int k) {
+        const T coef = vcoef[jj % 3];
+        if (coef == T(0)) return;
+        const T* v = vbuf[jj % 3];
+        T* col = Xs + (size_t)k * m;
+        T xr[RPL], vr[RPL];
+        T d = 0;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          const int i = lane + 32 * t;
+          xr[t] = i < m ? col[i] : T(0);
+          vr[t] = i < m ? v[i] : T(0);
+          d += vr[t] * xr[t];
+        }
+        d = warp_sum(d) * coef;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+          const int i = lane + 32 * t;
+          if (i < m) col[i] = xr[t] - d * vr[t];
+        }
+      };
+      // reflector jj applied to every column k > lo this warp owns: the dot products of all of
+      // them are reduced in one interleaved butterfly instead of one reduction after another
+      auto apply_batch = [&](int jj, int lo) {
+        const T coef = vcoef[jj % 3];
+        if (coef == T(0)) return;
+        const T* v = vbuf[jj % 3];
+        T vr[RPL], d[CPW];
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) { const int i = lane + 32 * t; vr[t] = i < m ? v[i] : T(0); }
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+          const int k = warp + NWARP * q;
+          d[q] = 0;
+          if (k > lo && k < D) {
+            const T* col = Xs + (size_t)k * m;
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) { const int i = lane + 32 * t; if (i < m) d[q] += vr[t] * col[i]; }
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int q = 0; q < CPW; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+#pragma unroll
+        for (int q = 0; q < CPW; ++q) {
+          const int k = warp + NWARP * q;
+          if (k > lo && k < D) {
+            T* col = Xs + (size_t)k * m;
+            const T dc = d[q] * coef;
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) { const int i = lane + 32 * t; if (i < m) col[i] -= dc * vr[t]; }
+          }
+        }
+      };
+      // Step j: the owner of column j+1 applies reflector j to that column and forms reflector
+      // j+1 at once (the critical path), deferring its other columns to the next step; every
+      // other warp applies reflector j to its columns.  Reflectors rotate through three slots,
+      // so a deferred one is still intact when its owner applies it.
       if (warp == 0) house(0);
+      int pend = -1;                  // reflector this warp still owes its columns > pend + 1
       for (int j = 0; j < D; ++j) {
         __syncthreads();
-        const T coef = vcoef[j & 1];
-        const T* v = vbuf[j & 1];
-        auto apply = [&](int k) {
-          T* col = Xs + (size_t)k * m;
-          T xr[RPL], vr[RPL];
-          T d = 0;
-#pragma unroll
-          for (int t = 0; t < RPL; ++t) {
-            const int i = lane + 32 * t;
-            xr[t] = i < m ? col[i] : T(0);
-            vr[t] = i < m ? v[i] : T(0);
-            d += vr[t] * xr[t];
-          }
-          d = warp_sum(d) * coef;
-#pragma unroll
-          for (int t = 0; t < RPL; ++t) {
-            const int i = lane + 32 * t;
-            if (i < m) col[i] = xr[t] - d * vr[t];
-          }
-        };
-        // the owner of column j+1 updates it first and forms the next reflector at once;
-        // every other column of this warp is updated afterwards (needed only later)
+        if (pend >= 0) { apply_batch(pend, pend + 1); pend = -1; }
         const int nxt = j + 1;
-        const bool owner = nxt < D && warp == nxt % NWARP;
-        if (owner) {
-          if (coef != T(0)) apply(nxt);
+        if (nxt < D && warp == nxt % NWARP) {
+          apply1(j, nxt);
           __syncwarp();
           house(nxt);
-        }
-        if (coef != T(0)) {
-          for (int k = j + 1 + ((warp - (j + 1)) % NWARP + NWARP) % NWARP; k < D; k += NWARP)
-            if (!(owner && k == nxt)) apply(k);
+          pend = j;
+        } else {
+          apply_batch(j, j);
         }
         __syncwarp();
       }
@@ -553,30 +593,37 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
         const int wj = tid >> 5, grp = (tid >> 3) & 3, li = tid & 7;
         const int NB = npad / 4, mb = NB - 1;
         const bool wact = wj < NB / 2;
-        auto jpair = [&](int p, int q) {
-          V16* yp = reinterpret_cast<V16*>(Yc + (size_t)p * DP);
-          V16* yq = reinterpret_cast<V16*>(Yc + (size_t)q * DP);
-          V16* vp = reinterpret_cast<V16*>(Vc + (size_t)p * DP);
-          V16* vq = reinterpret_cast<V16*>(Vc + (size_t)q * DP);
-          V16 up[NV], uq[NV], wp[NV], wq[NV];
+        // The sweep is bound by shared-memory traffic at the occupancy the build runs at, so a
+        // pair's V columns are read only when the pair rotates, and in the cross sub-rounds
+        // each 8-lane group keeps its block-A column (Y and V) in registers.
+        auto rotation = [&](const V16* u, const V16* w, T& cs, T& sn) -> bool {
           T g = 0, a = 0, b = 0;
 #pragma unroll
           for (int k = 0; k < NV; ++k) {
-            up[k] = yp[li + 8 * k];
-            uq[k] = yq[li + 8 * k];
-            wp[k] = vp[li + 8 * k];     // issued early: their latency overlaps the reductions
-            wq[k] = vq[li + 8 * k];
-          }
-#pragma unroll
-          for (int k = 0; k < NV; ++k) {
-            g += dot16(up[k], uq[k]);
-            a += dot16(up[k], up[k]);
-            b += dot16(uq[k], uq[k]);
+            g += dot16(u[k], w[k]);
+            a += dot16(u[k], u[k]);
+            b += dot16(w[k], w[k]);
           }
           g = group8_sum(g); a = group8_sum(a); b = group8_sum(b);
           if (a > tinyY && b > tinyY && g * g > tol * tol * a * b) {
-            T cs, sn;
             rotation_from_gram(a, b, g, cs, sn);
+            return true;
+          }
+          return false;
+        };
+        auto jpair = [&](int p, int q) {          // both columns from shared memory
+          V16* yp = reinterpret_cast<V16*>(Yc + (size_t)p * DP);
+          V16* yq = reinterpret_cast<V16*>(Yc + (size_t)q * DP);
+          V16 up[NV], uq[NV];
+#pragma unroll
+          for (int k = 0; k < NV; ++k) { up[k] = yp[li + 8 * k]; uq[k] = yq[li + 8 * k]; }
+          T cs, sn;
+          if (rotation(up, uq, cs, sn)) {
+            V16* vp = reinterpret_cast<V16*>(Vc + (size_t)p * DP);
+            V16* vq = reinterpret_cast<V16*>(Vc + (size_t)q * DP);
+            V16 wp[NV], wq[NV];
+#pragma unroll
+            for (int k = 0; k < NV; ++k) { wp[k] = vp[li + 8 * k]; wq[k] = vq[li + 8 * k]; }
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
               rot16(up[k], uq[k], cs, sn);
@@ -595,7 +642,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
           // thread read a flag that was already cleared and leave the loop alone)
           if (tid == 0) rot[(sweep + 1) % 3] = 0;
           for (int br = 0; br < mb; ++br) {
-            if (wact) {       // warp-uniform: the shuffles of jpair need the whole warp
+            if (wact) {       // warp-uniform: the shuffles of the reductions need the whole warp
               // block pair of slot wj (circle method: slot 0 keeps block NB-1)
               const int bA = wj == 0 ? NB - 1 : (br + wj) % mb;
               const int bB = wj == 0 ? br : (br - wj + mb) % mb;
@@ -611,10 +658,47 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
                   __syncwarp();
                 }
               }
+              // cross pairs: group grp holds column A = 4 bA + grp and meets the four columns
+              // of block B in turn (B column (grp + t) mod 4 in sub-round t)
+              const int pa = 4 * bA + grp;
+              V16* ya_s = reinterpret_cast<V16*>(Yc + (size_t)pa * DP);
+              V16* va_s = reinterpret_cast<V16*>(Vc + (size_t)pa * DP);
+              V16 ya[NV], va[NV];
+#pragma unroll
+              for (int k = 0; k < NV; ++k) ya[k] = ya_s[li + 8 * k];
+              bool va_held = false;   // group-uniform: every lane of a group sees the same sums
 #pragma unroll 1
               for (int t = 0; t < 4; ++t) {
-                jpair(4 * bA + grp, 4 * bB + ((grp + t) & 3));
+                const int q = 4 * bB + ((grp + t) & 3);
+                V16* yq = reinterpret_cast<V16*>(Yc + (size_t)q * DP);
+                V16 uq[NV];
+#pragma unroll
+                for (int k = 0; k < NV; ++k) uq[k] = yq[li + 8 * k];
+                T cs, sn;
+                if (rotation(ya, uq, cs, sn)) {
+                  V16* vq = reinterpret_cast<V16*>(Vc + (size_t)q * DP);
+                  V16 wq[NV];
+                  if (!va_held) {
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) va[k] = va_s[li + 8 * k];
+                    va_held = true;
+                  }
+#pragma unroll
+                  for (int k = 0; k < NV; ++k) wq[k] = vq[li + 8 * k];
+#pragma unroll
+                  for (int k = 0; k < NV; ++k) {
+                    rot16(ya[k], uq[k], cs, sn);
+                    rot16(va[k], wq[k], cs, sn);
+                    yq[li + 8 * k] = uq[k];
+                    vq[li + 8 * k] = wq[k];
+                  }
+                  if (li == 0) rot[sweep % 3] = 1;
+                }
                 __syncwarp();
+              }
+              if (va_held) {          // column A changed: back to shared memory
+#pragma unroll
+                for (int k = 0; k < NV; ++k) { ya_s[li + 8 * k] = ya[k]; va_s[li + 8 * k] = va[k]; }
               }
             }
             named_barrier(1, NJ);

@@ -6,7 +6,8 @@ import numpy as np
 import pytest
 
 from oracle import brute, lattice, metropolis, sampler
-from tests.gpu_helpers import ABS_REDUCED, REL_FP64, assert_qplus_close, check_spins_match, oracle_envs
+from tests.gpu_helpers import (ABS_REDUCED, REL_FP64, assert_logq_within_site_tolerance, assert_qplus_close,
+                               check_spins_match, oracle_envs)
 
 pytestmark = pytest.mark.gpu
 
@@ -118,12 +119,13 @@ def test_conditionals_and_spins(tn, precision, L, chi, p):
         for ch in range(2):
             ev = sampler.evaluate(env, spins[k, ch])
             assert_qplus_close(qp_tf[k, ch], ev["qplus"], precision)
-            rel = 1e-9 if precision == "fp64" else None
-            if rel:
-                assert np.abs(lq[k, ch] - ev["logq"]).max() <= rel * np.abs(ev["logq"]).max() + 1e-10
-                assert np.abs(lq_tf[k, ch] - ev["logq"]).max() <= rel * np.abs(ev["logq"]).max() + 1e-10
+            # the chain uses exactly the q it sampled from: a proposal's log q equals the same
+            # kernel's teacher-forced log q of its own spins on every path
+            assert np.abs(lq[k, ch] - lq_tf[k, ch]).max() <= 1e-9 * np.abs(lq_tf[k, ch]).max() + 1e-12
+            if precision == "fp64":
+                assert np.abs(lq[k, ch] - ev["logq"]).max() <= REL_FP64 * np.abs(ev["logq"]).max() + 1e-10
             else:
-                assert np.abs(lq[k, ch] - ev["logq"]).max() <= 1e-3 * L * L
+                assert_logq_within_site_tolerance(lq[k, ch], ev["logq"], ev["qplus"], spins[k, ch], qp_tf[k, ch])
             Jh, Jv = lattice.split_couplings(lattice.couplings_pmj(s, L, p), L)
             assert np.array_equal(E[k, ch], lattice.energy(spins[k, ch], Jh, Jv))
             assert np.array_equal(M[k, ch], spins[k, ch].reshape(n, -1).sum(axis=1))
@@ -303,4 +305,41 @@ def test_argument_errors(tn):
     with pytest.raises(_capi.TnmcError) as e:
         ctx.accept()
     assert e.value.code == 6
+    ctx.close()
+
+
+@pytest.mark.parametrize("L,seed", [
+    (128, 77),
+    pytest.param(256, 1_000_003, marks=pytest.mark.xfail(
+        strict=True, reason="FP32-built environments give conditionals 5.5e-3 from the FP64 oracle at L = 256 "
+                            "(measured; the FP32 Householder R factors lose the small singular directions)")),
+])
+def test_large_lattice_parity_tf32(tn, L, seed):
+    """The configuration the throughput is quoted on (chi = 32, p = 0.109, mixed TF32) at L = 128
+    and 256: teacher-forced q(+) at every site of the GPU's own proposals within 1e-3 of the FP64
+    oracle, log q within the bound that per-site tolerance implies, proposal log q equal to the
+    teacher-forced one, and the spins equal to the oracle's own draws wherever |u - q(+)| exceeds
+    the tolerance.  One realization, two chains x two proposals (the oracle needs about a minute
+    per L = 256 realization on the host)."""
+    p, chi, n = 0.109, 32, 2
+    ctx = _ctx(tn, L, p, chi, [seed], "tf32")
+    ctx.build_env(return_logz=False)
+    out = ctx.propose(n, 3)
+    spins = ctx.spins().cpu().numpy()
+    lq = out["logq"].cpu().numpy()
+    E = out["energy"].cpu().numpy()
+    lq_tf, qp_tf = ctx.eval_conditionals(torch.from_numpy(spins.reshape(1, 2 * n, L, L)).cuda())
+    lq_tf = lq_tf.cpu().numpy().reshape(2, n)
+    qp_tf = qp_tf.cpu().numpy().reshape(2, n, L, L)
+    assert np.all(ctx.realization_status() == 0)
+    env = oracle_envs(seed, L, p, chi)
+    Jh, Jv = lattice.split_couplings(lattice.couplings_pmj(seed, L, p), L)
+    for ch in range(2):
+        ev = sampler.evaluate(env, spins[0, ch])
+        err = assert_qplus_close(qp_tf[ch], ev["qplus"], "tf32")
+        print(f"L={L}: chain {ch} max |dq(+)| = {err:.3e}")
+        assert np.abs(lq[0, ch] - lq_tf[ch]).max() <= 1e-9 * np.abs(lq_tf[ch]).max()
+        assert_logq_within_site_tolerance(lq[0, ch], ev["logq"], ev["qplus"], spins[0, ch], qp_tf[ch])
+        assert np.array_equal(E[0, ch], lattice.energy(spins[0, ch], Jh, Jv))
+        check_spins_match(env, seed, ch, np.arange(3, 3 + n), spins[0, ch], ev["qplus"], ABS_REDUCED)
     ctx.close()
