@@ -28,9 +28,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# measured DRAM traffic per unit of work (ncu, see roofline())
-ENV_DRAM_BYTES_PER_SITE_STEP = 6372628736 / (16 * 127 * 128)           # 24.5 KB
-SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE = 64751584768 / (16 * 500 * 128 * 128)   # 494 B
+# DRAM bytes per unit of work from one ncu capture of the current kernels (see roofline());
+# None until a capture of these kernels exists
+ENV_DRAM_BYTES_PER_SITE_STEP = None
+SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE = None
 
 METRIC = "spins proposed/s at L=256 χ=32, BF16/TF32 vs FP64 GPU path; p50/p99 latency"
 UNIT = "spins/s"
@@ -52,6 +53,8 @@ def parse():
     ap.add_argument("--p", type=float, default=0.109)
     ap.add_argument("--inflight", type=int, default=0,
                     help="batches in flight (contexts on streams); 0 = as many as the SMs hold at once")
+    ap.add_argument("--obs-out", default=None,
+                    help="write the per-realization thermal means of the last batch of every context (JSON)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
@@ -364,8 +367,13 @@ def main():
     failed_seeds = [int(seeds_for(k)[r]) for k in range(a.warmup + a.steps) for r in range(R) if fl[k, r] != 0]
     n_failed_timed = int((fl[a.warmup:] != 0).sum())
     obs = []        # the last batch of every context (observables of the realizations it holds)
-    for c in ctxs:
+    obs_seeds = []
+    for i, c in enumerate(ctxs):
         obs += c.observables(allow_numeric=True)
+        obs_seeds += [int(x) for x in seeds_for(step_of[i])]
+    if a.obs_out and rank == 0:
+        with open(a.obs_out, "w") as f:
+            json.dump([dict(o, seed=sd) for o, sd in zip(obs, obs_seeds)], f)
     if world > 1:       # the one cross-rank exchange: per-realization means for [.] averages
         from paper_2409_06538_gb300 import shard
         dav, _ = shard.gather_disorder_average(obs, L, beta)
@@ -454,13 +462,15 @@ def main():
 
 
 def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
-    """Roofline of the dominant kernel from live CUDA-event timings.  Algorithmic work per
-    launch of the environment build: per site step the MPO product X (8 D^2 CHI flops),
-    the Householder R factor of the 2D x D matrix (10/3 D^3), Q (4 CHI^3), Y = R M (2 D^3),
-    P = M V (2 D^2 CHI) and the one-sided Jacobi SVD at the measured mean sweep count
-    (per sweep D(D-1)/2 pairs x (3 dot products + rotation of two Y and two V columns =
-    12 D + 6 D flops)).  Sampling sweep: bytes of the environment tiles read twice per row
-    per 128-proposal tile plus the per-site workspace written and read back."""
+    """Roofline of the dominant kernel from live CUDA-event timings.  Algorithmic work of the
+    environment build per site step (the boundary-MPS compression count of the method, not of this
+    implementation's iterations): Householder QR of the 4chi x 2chi matrix ~27 chi^3, the MPO
+    product R A ~32 chi^3, the truncating SVD of the 2chi x 2chi matrix ~100 chi^3 and the
+    product carrying the truncated state on ~16 chi^3, i.e. 175 chi^3 flops, times (L-1) L site
+    steps per realization.  It runs on the FP32 (FP64) CUDA cores, so the peak is the ALU peak
+    derived from 152 SMs x 128 FP32 lanes x 2 flops x the SM clock (a 64th of it for FP64).
+    Sampling sweep: bytes of the environment tiles read twice per row per 128-proposal tile plus
+    the per-site workspace written and read back, against the measured HBM copy bandwidth."""
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -468,10 +478,8 @@ def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     L, chi = a.L, a.chi
-    CHI = 4 if chi <= 4 else 8 if chi <= 8 else 16 if chi <= 16 else 32
-    D = 2 * CHI
-    site_flops = (8 * D * D * CHI + (10.0 / 3.0) * D ** 3 + 4 * CHI ** 3 + 2 * D ** 3 + 2 * D * D * CHI
-                  + mean_sweeps * (D * (D - 1) / 2) * (18 * D))
+    CHI = 4 if chi <= 4 else 8 if chi <= 8 else 16 if chi <= 16 else 32 if chi <= 32 else 64
+    site_flops = 175.0 * chi ** 3
     build_flops = a.R * (L - 1) * L * site_flops                  # per launch (one batch)
     K = len(marks)
     sm_clock = peaks.get("sm_max_mhz", 2070.0) * 1e6
@@ -486,21 +494,21 @@ def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
     tiles = math.ceil(items / M) * a.R
     samp_bytes = tiles * 2 * L * L * (2 * CHI * CHI) * te + a.R * items * L * L * (2 * CHI) * 4 * 2
     samp_gbs = K * samp_bytes / (samp_union_ms / 1e3) / 1e9
-    # DRAM bytes per unit from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of
-    # profile_case 128 32 16 tf32 250, L2-exceeding; profiles/dram_traffic_L128_chi32_R16_tf32.md),
-    # scaled by the units of one launch here; only for the kernels that capture measured
     env_traffic = samp_traffic = None
     if a.precision == "tf32" and CHI == 32:
-        env_traffic = ENV_DRAM_BYTES_PER_SITE_STEP * a.R * (L - 1) * L
-        samp_traffic = SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE * a.R * items * L * L
+        if ENV_DRAM_BYTES_PER_SITE_STEP is not None:
+            env_traffic = ENV_DRAM_BYTES_PER_SITE_STEP * a.R * (L - 1) * L
+        if SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE is not None:
+            samp_traffic = SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE * a.R * items * L * L
     return dict(kernel="env_build_kernel", bound="alu", achieved=build_tf, peak=alu_peak, unit="TFLOP/s",
                 frac=build_tf / alu_peak, traffic=env_traffic,
                 traffic_source=("ncu capture at L=128, 16 realizations, scaled per site step"
                                 if env_traffic is not None else None),
                 peak_source=("derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
                              + (" / 64 (FP64 rate of this part)" if a.precision == "fp64" else "")),
-                algorithmic_flops_per_launch=build_flops, launches=K,
-                per_launch_ms=per_launch_ms, busy_ms=build_union_ms,
+                algorithmic_flops_per_site_step=site_flops, algorithmic_flops_per_launch=build_flops,
+                launches=K, per_launch_ms=per_launch_ms, busy_ms=build_union_ms,
+                jacobi_mean_sweeps=mean_sweeps,
                 sampler=dict(kernel="sample_tc_kernel" if M == 128 else "sample_kernel", bound="hbm",
                              achieved=samp_gbs, peak=hbm, unit="GB/s", frac=samp_gbs / hbm,
                              algorithmic_bytes_per_launch=samp_bytes, busy_ms=samp_union_ms,

@@ -23,14 +23,17 @@
 
 namespace tnmc {
 
-// Convergence: a pair counts as orthogonal when |y_p . y_q| <= tol |y_p| |y_q|.  The
-// rounding floor of a D-long dot product is about sqrt(D) eps, so tol = 4 sqrt(D) eps
-// (the criterion of one-sided Jacobi SVD codes, scaled for a safety margin).
+// Convergence: a pair counts as orthogonal when |y_p . y_q| <= tol |y_p| |y_q|, with tol =
+// sqrt(D) eps, the rounding floor of a D-long dot product.  The residual non-orthogonality
+// tilts the kept singular subspace where sigma_chi and sigma_{chi+1} are close; in FP32 at
+// L = 256, chi = 32 a four times looser tolerance left environments whose conditionals drifted
+// by up to 5e-3 from FP64 and produced doubly clamped sites (measured), for about 1 % more
+// sweeps it does not.
 template <typename T> struct JacobiTol;
 template <> struct JacobiTol<float> { static constexpr int maxsw = 30; };
 template <> struct JacobiTol<double> { static constexpr int maxsw = 40; };
 template <typename T, int D> __device__ __forceinline__ T jacobi_tol() {
-  return T(4) * num<T>::sqrt_(T(D)) * num<T>::eps;
+  return num<T>::sqrt_(T(D)) * num<T>::eps;
 }
 
 template <typename T> struct Vec16;
@@ -292,10 +295,15 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
             for (int jj = 0; jj < 4; ++jj) acc[ii][jj] += rw * bv[jj];
           }
         }
+        // row (x, i) of X is stored at 2 i + x: the two blocks R_c A^0 and R_c A^1 share
+        // R_c's row scale, which falls with i, so interleaving them lets the reflectors meet
+        // the rows in order of scale (measured at L = 256 in FP32: two orders of magnitude
+        // fewer clamped weights than the two blocks one after the other)
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
-          const T col4[4] = {acc[0][jj], acc[1][jj], acc[2][jj], acc[3][jj]};
-          st4(Xs + (size_t)(b * CHI + b0 + jj) * (2 * D) + x * D + i0, col4);
+          T* xc = Xs + (size_t)(b * CHI + b0 + jj) * (2 * D);
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) xc[2 * (i0 + ii) + x] = acc[ii][jj];
         }
       }
       __syncthreads();
