@@ -1,4 +1,5 @@
-"""GPU checks of the measurement tools: the pilot-based bond-dimension choice."""
+"""GPU checks of the tools around the method: the pilot-based bond-dimension choice, the bounded-wait
+failure detection and the caller-supplied device allocator."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -45,3 +46,33 @@ def test_bounded_wait_times_out_and_the_context_survives(tn):
     t.accept()
     assert all(o["n_prop"] == 16 for o in t.observables())
     t.close()
+
+
+def test_device_memory_comes_from_the_callers_allocator():
+    """With the Python binding's default allocator every device buffer of a context comes from
+    PyTorch's caching allocator through tnmc_opts.alloc/free (PyTorch's count grows by at least
+    the context's bytes and falls back when it is destroyed); with allocator="library" the
+    library allocates on its own and PyTorch's count does not move."""
+    import paper_2409_06538_gb300 as tn
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    tn.build()
+    L, chi, p = 16, 8, 0.109
+    beta = tn.nishimori_beta(p)
+    seeds = [3, 4]
+    J = tn.couplings_pmj(L, seeds, p)
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    ctx = tn.TNMC(L, J, [beta] * 2, seeds, chi, precision="fp32")
+    held = ctx.device_bytes()
+    assert torch.cuda.memory_allocated() - base >= held > 0
+    ctx.build_env()
+    ctx.propose(4, 0)
+    ctx.accept()
+    assert all(o["status"] == 0 for o in ctx.observables())
+    ctx.close()
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == base
+    ctx = tn.TNMC(L, J, [beta] * 2, seeds, chi, precision="fp32", allocator="library")
+    assert torch.cuda.memory_allocated() == base
+    ctx.close()
