@@ -18,6 +18,8 @@ QR / SVD as library steps:
                     evaluated in reverse contraction order with fixed spins as fields.
 * ``metropolis``    Eq. (accptanceratio) and the independence-sampler form of App. A.
 * ``observables``   Sec. III.C: energy, magnetisation, two-replica overlap, Binder ratios.
+* ``periodic``      Sec. IV: periodic boundaries by a pinned pair of lines per step, the
+                    rest of the torus sampled as an open region with the fixed spins as fields.
 * ``brute``         exhaustive enumeration used to pin all of the above on small lattices.
 
 Parity status: every function is pinned by the ``-m "not gpu"`` tests in ``tests/``

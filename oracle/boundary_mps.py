@@ -25,11 +25,12 @@ import numpy as np
 SV = np.array([1.0, -1.0])   # spin value of tensor index 0 / 1
 
 
-def row_mpo(beta, jv_row, jh_below):
+def row_mpo(beta, jv_row, jh_below, h_below=None):
     """MPO of one row transfer: O[c][a, x, y, b] for the upper spin x (row r), the lower
     spin y (row r+1), left MPO bond a = y_{c-1} and right MPO bond b = y_c.
 
-    jv_row: Jv[r, :] (Lx,), jh_below: Jh[r+1, :] (Lx-1,).
+    jv_row: Jv[r, :] (Lx,), jh_below: Jh[r+1, :] (Lx-1,); h_below: optional external fields
+    on the spins of row r+1 (Lx,), entering as the site weight exp(h s(y)).
     """
     Lx = len(jv_row)
     ops = []
@@ -43,6 +44,8 @@ def row_mpo(beta, jv_row, jh_below):
                     val = np.exp(beta * jv_row[c] * SV[x] * SV[y])
                     if c > 0:
                         val *= np.exp(beta * jh_below[c - 1] * SV[a] * SV[y])
+                    if h_below is not None:
+                        val *= np.exp(h_below[c] * SV[y])
                     if c < Lx - 1:
                         O[a, x, y, y] = val          # delta_{b, y}: pass y_c to the right
                     else:
@@ -89,11 +92,12 @@ def compress(A, chi):
 
 
 class Envs:
-    """Cached row environments: B[r][c] (k_c, 2, k_{c+1}), lam[r], log_z."""
+    """Cached row environments: B[r][c] (k_c, 2, k_{c+1}), lam[r], log_z, and the external
+    fields H (Ly, Lx) the network was built with (None: no fields)."""
 
-    def __init__(self, B, lam, log_z, Jh, Jv, beta, chi):
+    def __init__(self, B, lam, log_z, Jh, Jv, beta, chi, H=None):
         self.B, self.lam, self.log_z = B, lam, log_z
-        self.Jh, self.Jv, self.beta, self.chi = Jh, Jv, beta, chi
+        self.Jh, self.Jv, self.beta, self.chi, self.H = Jh, Jv, beta, chi, H
 
     @property
     def Ly(self):
@@ -107,29 +111,32 @@ class Envs:
         return [b.shape[0] for b in self.B[r]] + [1]
 
 
-def build_envs(Jh, Jv, beta, chi):
-    """All row environments of the Ly x Lx lattice (Jh (Ly, Lx-1), Jv (Ly-1, Lx))."""
+def build_envs(Jh, Jv, beta, chi, H=None):
+    """All row environments of the Ly x Lx lattice (Jh (Ly, Lx-1), Jv (Ly-1, Lx)), optionally
+    with external fields H (Ly, Lx): the weight of a configuration gains exp(sum H s)."""
     Jh = np.asarray(Jh, dtype=np.float64)
     Jv = np.asarray(Jv, dtype=np.float64)
+    H = None if H is None else np.asarray(H, dtype=np.float64)
     Ly, Lx = Jh.shape[0], Jh.shape[1] + 1
     B = [None] * Ly
     lam = np.zeros(Ly)
     B[Ly - 1] = [np.ones((1, 2, 1)) for _ in range(Lx)]
     for r in range(Ly - 2, -1, -1):
-        A = apply_mpo(row_mpo(beta, Jv[r], Jh[r + 1]), B[r + 1])
+        A = apply_mpo(row_mpo(beta, Jv[r], Jh[r + 1], None if H is None else H[r + 1]), B[r + 1])
         B[r], lam[r] = compress(A, chi)
-    log_z = float(lam.sum()) + log_row_sum(B[0], Jh[0], beta)
-    return Envs(B, lam, log_z, Jh, Jv, beta, chi)
+    log_z = float(lam.sum()) + log_row_sum(B[0], Jh[0], beta, None if H is None else H[0])
+    return Envs(B, lam, log_z, Jh, Jv, beta, chi, H)
 
 
-def log_row_sum(mps, jh_row, beta):
-    """log sum_x prod_c exp(beta Jh[0,c] s(x_c) s(x_{c+1})) Gt_0(x): closes the network
-    on the top row (Eq. Z)."""
-    ell = mps[0][0]                          # (2, k1): left vector for each x_0
+def log_row_sum(mps, jh_row, beta, h_row=None):
+    """log sum_x prod_c exp(beta Jh[0,c] s(x_c) s(x_{c+1}) + h[c] s(x_c)) Gt_0(x): closes the
+    network on the top row (Eq. Z), with the top row's own fields when given."""
+    f = (lambda c: np.ones(2)) if h_row is None else (lambda c: np.exp(h_row[c] * SV))
+    ell = mps[0][0] * f(0)[:, None]          # (2, k1): left vector for each x_0
     logs = 0.0
     for c in range(1, len(mps)):
         W = np.exp(beta * jh_row[c - 1] * np.outer(SV, SV))     # W[x', x]
-        ell = np.einsum('pa,px,axb->xb', ell, W, mps[c])
+        ell = np.einsum('pa,px,axb->xb', ell, W, mps[c]) * f(c)[:, None]
         m = np.abs(ell).max()
         ell = ell / m
         logs += np.log(m)

@@ -34,14 +34,17 @@ def row_configs(Lx):
     return 1 - 2 * bits                     # (2**Lx, Lx)
 
 
-def exact(Jh, Jv, beta):
-    """(states, energies, log Z, probabilities) by enumeration."""
+def exact(Jh, Jv, beta, H=None):
+    """(states, energies, log Z, probabilities) by enumeration; with fields H (Ly, Lx) the
+    weight is exp(-beta E(s) + sum H s)."""
     Jh = np.asarray(Jh).astype(np.int64)
     Jv = np.asarray(Jv).astype(np.int64)
     Ly, Lx = Jh.shape[0], Jh.shape[1] + 1
     S = all_states(Ly, Lx)
     E = lattice.energy(S, Jh, Jv)
     a = -beta * E
+    if H is not None:
+        a = a + (S * np.asarray(H, dtype=np.float64)[None]).sum(axis=(1, 2))
     amax = a.max()
     logZ = amax + np.log(np.exp(a - amax).sum())
     return S, E, logZ, np.exp(a - logZ)

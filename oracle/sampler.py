@@ -6,7 +6,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 Spins are drawn row by row, top to bottom, each row left to right (sites numbered from
 the top left to the bottom right, Sec. II.B).  For row r the fixed spins of row r-1 act
 through the vertical Boltzmann matrices as external fields h_c = beta Jv[r-1,c] s_{r-1,c}
-(Fig. fig:Z4).  The process tensors of row r are contracted from the right to the left
+(Fig. fig:Z4); external fields of the network (the fixed lines of a periodic step) add to
+them.  The process tensors of row r are contracted from the right to the left
 with those fields (the right sweep), then each spin's conditional partition function is
 the left part with fixed spins, the site tensor and the right part, times the bond
 factor to the spin on its left (Fig. fig:ZS4):
@@ -99,6 +100,8 @@ def propose(envs, seed, chain, steps):
     cols = np.arange(Lx, dtype=np.uint64)
     for r in range(Ly):
         h = np.zeros((K, Lx)) if r == 0 else envs.beta * envs.Jv[r - 1][None, :] * spins[:, r - 1, :]
+        if envs.H is not None:
+            h = h + envs.H[r][None, :]
         site = np.uint64(r * Lx) + cols
         u = philox.uniform(seed, site[None, :], steps[:, None], chain, philox.PURPOSE_SPIN)
         s, lq, qp, cl = sweep_row(envs.B[r], envs.Jh[r], h, envs.beta, uniforms=u)
@@ -119,6 +122,8 @@ def evaluate(envs, spins):
     clamps = np.zeros(K, dtype=np.int64)
     for r in range(Ly):
         h = np.zeros((K, Lx)) if r == 0 else envs.beta * envs.Jv[r - 1][None, :] * spins[:, r - 1, :]
+        if envs.H is not None:
+            h = h + envs.H[r][None, :]
         _, lq, qp, cl = sweep_row(envs.B[r], envs.Jh[r], h, envs.beta, forced=spins[:, r, :])
         qplus[:, r, :] = qp
         logq += lq

@@ -119,3 +119,21 @@ def test_coupling_generator_layout_and_rate():
     assert np.array_equal(J2, np.where(u < p, -1, 1).astype(np.int8))
     Jh, Jv = lattice.split_couplings(J2, 8)
     assert Jh.shape == (8, 7) and Jv.shape == (7, 8)
+
+
+@pytest.mark.parametrize("Ly,Lx", [(3, 3), (4, 4), (2, 5)])
+def test_untruncated_with_external_fields(Ly, Lx):
+    """External fields H (weight exp(-beta E + sum H s)): untruncated environments give
+    log Z and q(s) = P(s) of the enumerated distribution with fields, and the fields matter
+    (the distribution differs from the field-free one)."""
+    rng = np.random.default_rng(Ly * 7 + Lx)
+    Jh, Jv = _random_bonds(Ly, Lx, 0.2, rng)
+    H = rng.normal(0.0, 0.7, (Ly, Lx))
+    beta = 0.85
+    env = bm.build_envs(Jh, Jv, beta, 2 ** (Lx // 2), H)
+    S, E, logZ, P = brute.exact(Jh, Jv, beta, H)
+    assert abs(env.log_z - logZ) < 1e-11 * max(1.0, abs(logZ))
+    ev = sampler.evaluate(env, S)
+    assert np.abs(np.exp(ev["logq"]) - P).max() < 1e-12
+    _, _, _, P0 = brute.exact(Jh, Jv, beta)
+    assert np.abs(P - P0).max() > 1e-3
