@@ -198,6 +198,13 @@ tnmc_status tnmc_build_env(tnmc_ctx* ctx, double* log_z_host);
 tnmc_status tnmc_propose(tnmc_ctx* ctx, int n, uint64_t step0, double* logq_dev,
                          int32_t* energy_dev, int32_t* magnet_dev);
 
+/* External fields (the paper's fixed spins of Sec. IV act this way): fields (host or device,
+ * n_real * L * L int8, [real][r][c]) are integers k in units of beta, so that a configuration's
+ * weight gains exp(beta sum_i k_i s_i); they enter the row MPO of the environments (the row below
+ * each row) and the fields of the sampling sweep.  The environments become stale (build again).
+ * NULL removes the fields.  Errors: TNMC_ERR_ARG, TNMC_ERR_OOM, TNMC_ERR_CUDA. */
+tnmc_status tnmc_set_fields(tnmc_ctx* ctx, const int8_t* fields);
+
 /* Unpack the spins of the last tnmc_propose call to spins_dev (device int8 +-1,
  * [real][chain][k][L*L]). */
 tnmc_status tnmc_get_spins(tnmc_ctx* ctx, int8_t* spins_dev);
@@ -326,6 +333,53 @@ tnmc_status tnmc_env_build_occupancy(int L, int chi, int precision, int32_t* cta
  * 152 when no device is present. */
 size_t tnmc_device_bytes(const tnmc_ctx* ctx);
 size_t tnmc_estimate_device_bytes(int L, int n_real, int chi, const tnmc_opts* opts, int n_max);
+
+/* ------------------------------------------------------------------------------------------
+ * Periodic boundaries (Sec. IV): each step of each chain pins a row i0 and a column j0 of the
+ * L x L torus, keeps their spins fixed, and samples the remaining (L-1) x (L-1) region as an
+ * open lattice whose fixed neighbours act as external fields; the proposal replaces the region
+ * with the Metropolis probability of the region's conditional distribution given the lines,
+ *   Delta = [-beta E_reg(x') + beta k.x' - log q(x')] - [-beta E_reg(x) + beta k.x - log q(x)],
+ * so every step leaves the torus Boltzmann distribution invariant.  The environments depend on
+ * the fixed spins and are rebuilt for every step of every chain (one proposal per build).
+ * Torus couplings of one realization: 2 L^2 int8 +-1, first Jh[r][c] coupling (r, c)-(r, c+1 mod L)
+ * row-major, then Jv[r][c] coupling (r, c)-(r+1 mod L, c) row-major.  Lines of step t of chain k:
+ * i0 = floor(u L), j0 = floor(u' L) with u, u' the uniforms of counters (0, t, k, 3) and
+ * (1, t, k, 3); region site (r, c) is torus site (i0+1+r, j0+1+c) mod L, its spin draw uses the
+ * region's site index r (L-1) + c with counter (site, t, k, 1); the accept uniform is the counter
+ * (0, t, k, 2).  Chains start from all spins up.
+ * ------------------------------------------------------------------------------------------ */
+typedef struct tnmc_periodic tnmc_periodic;
+
+/* Seeded torus disorder: J_b = -1 iff u_b < p, u_b the uniform of counter (b, 0, 0, 0), for the
+ * 2 L^2 bonds of each of n_real realizations, written to out_dev (device).  L >= 3. */
+tnmc_status tnmc_torus_couplings_pmj(int L, int n_real, const uint64_t* seeds_host, double p,
+                                     int8_t* out_dev, void* stream);
+
+/* Context of n_real torus realizations (couplings host or device, n_real * 2 L^2), inverse
+ * temperatures, seeds and the bond dimension chi of the regions' environments; opts as for
+ * tnmc_create (n_chains chains per realization, the overlap between chains 0 and 1).  3 <= L.
+ * Errors as tnmc_create. */
+tnmc_status tnmc_periodic_create(int L, int n_real, const int8_t* couplings, const double* beta_host,
+                                 const uint64_t* seeds_host, int chi, const tnmc_opts* opts,
+                                 tnmc_periodic** out);
+
+/* n_steps steps of every chain (global step indices step0 ...); observables of the torus states
+ * (E with the periodic bonds, m, the overlap q) accumulate after every step with index >= n_therm.
+ * Asynchronous on the context's stream.  A region that meets a doubly clamped site flags its
+ * realization (tnmc_obs.status). */
+tnmc_status tnmc_periodic_step(tnmc_periodic* ctx, int n_steps, uint64_t step0);
+
+/* Per-realization thermal means of the torus (n_real tnmc_obs; m_edge fields are zero, the torus
+ * has no edge; n_tests = n_prop = steps x chains).  Synchronises. */
+tnmc_status tnmc_periodic_observables(tnmc_periodic* ctx, tnmc_obs* out_host);
+
+/* Current torus states to spins_dev (device int8 +-1, [real][chain][L*L]). */
+tnmc_status tnmc_periodic_get_spins(tnmc_periodic* ctx, int8_t* spins_dev);
+
+int64_t tnmc_periodic_launch_count(const tnmc_periodic* ctx);
+const char* tnmc_periodic_last_error(const tnmc_periodic* ctx);
+tnmc_status tnmc_periodic_destroy(tnmc_periodic* ctx);
 
 /* ------------------------------------------------------------------------------------------
  * Request server: continuous batching of independent realizations on one GPU.

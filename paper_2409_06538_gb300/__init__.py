@@ -3,4 +3,5 @@
 and the Metropolis correction, behind the C ABI of include/tnmc.h (libtnmc.so)."""
 from .buildlib import build, lib_path  # noqa: F401
 from .server import TNMCServer  # noqa: F401
-from .tnmc import TNMC, couplings_pmj, disorder_average, env_build_occupancy, nishimori_beta  # noqa: F401
+from .tnmc import (TNMC, TNMCPeriodic, couplings_pmj, disorder_average, env_build_occupancy,  # noqa: F401
+                   nishimori_beta, torus_couplings_pmj)

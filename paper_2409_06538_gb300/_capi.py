@@ -47,6 +47,16 @@ SIGNATURES = {
     "tnmc_disorder_average": (c_int, [c_void_p, c_int, c_int, c_double, c_void_p]),
     "tnmc_nishimori_beta": (c_int, [c_double, c_double_p]),
     "tnmc_estimate_device_bytes": (c_size_t, [c_int, c_int, c_int, c_void_p, c_int]),
+    "tnmc_set_fields": (c_int, [c_void_p, c_void_p]),
+    "tnmc_torus_couplings_pmj": (c_int, [c_int, c_int, c_uint64_p, c_double, c_void_p, c_void_p]),
+    "tnmc_periodic_create": (c_int, [c_int, c_int, c_void_p, c_double_p, c_uint64_p, c_int, c_void_p,
+                                     ctypes.POINTER(c_void_p)]),
+    "tnmc_periodic_step": (c_int, [c_void_p, c_int, ctypes.c_uint64]),
+    "tnmc_periodic_observables": (c_int, [c_void_p, c_void_p]),
+    "tnmc_periodic_get_spins": (c_int, [c_void_p, c_void_p]),
+    "tnmc_periodic_launch_count": (c_int64, [c_void_p]),
+    "tnmc_periodic_last_error": (ctypes.c_char_p, [c_void_p]),
+    "tnmc_periodic_destroy": (c_int, [c_void_p]),
     "tnmc_server_create": (c_int, [c_void_p, ctypes.POINTER(c_void_p)]),
     "tnmc_server_submit": (c_int, [c_void_p, c_void_p, c_int64_p]),
     "tnmc_server_poll": (c_int, [c_void_p, c_void_p, c_int]),

@@ -43,6 +43,9 @@ struct tnmc_ctx {
   long long* stats = nullptr;
   unsigned* status = nullptr;
   unsigned* rstatus = nullptr;    // per-realization status bits (numeric failures of its proposals)
+  int8_t* hfield = nullptr;       // external fields in units of beta, [real][L][L] (nullptr: none)
+  int8_t* hfield_buf = nullptr;   // the buffer behind hfield, allocated at the first tnmc_set_fields
+  const int* chain_of = nullptr;  // chain index of each realization's draws (periodic driver), or nullptr
   // sampling
   void* work = nullptr;
   void* work_tc = nullptr;        // workspace of the tensor-core sampler (mixed TF32 path)
@@ -417,6 +420,7 @@ tnmc_status tnmc_build_env(tnmc_ctx* c, double* log_z_host) {
     case TNMC_FP64: {
       tnmc::EnvBuildArgs<double, double> a{c->L, c->n_real, c->chi, c->J, c->beta, (double*)c->env, c->kdim, c->dqr,
                                            c->lam, c->logz, (double*)c->rowbuf, (double*)c->Rstore, c->stats, c->status};
+      a.hfield = c->hfield;
       e = tnmc::launch_env_build(a, c->CHI, c->stream);
       break;
     }
@@ -424,6 +428,7 @@ tnmc_status tnmc_build_env(tnmc_ctx* c, double* log_z_host) {
       tnmc::EnvBuildArgs<float, __nv_bfloat16> a{c->L, c->n_real, c->chi, c->J, c->beta, (__nv_bfloat16*)c->env, c->kdim,
                                                  c->dqr, c->lam, c->logz, (float*)c->rowbuf, (float*)c->Rstore, c->stats, c->status};
       a.Mscratch = (float*)c->mscratch;
+      a.hfield = c->hfield;
       e = tnmc::launch_env_build(a, c->CHI, c->stream);
       break;
     }
@@ -431,6 +436,7 @@ tnmc_status tnmc_build_env(tnmc_ctx* c, double* log_z_host) {
       tnmc::EnvBuildArgs<float, float> a{c->L, c->n_real, c->chi, c->J, c->beta, (float*)c->env, c->kdim, c->dqr,
                                          c->lam, c->logz, (float*)c->rowbuf, (float*)c->Rstore, c->stats, c->status};
       a.Mscratch = (float*)c->mscratch;
+      a.hfield = c->hfield;
       e = tnmc::launch_env_build(a, c->CHI, c->stream);
     }
   }
@@ -457,6 +463,8 @@ static tnmc_status run_sample(tnmc_ctx* c, int n, uint64_t step0, const int8_t* 
   a.clamps = props ? c->clamps : nullptr; a.forced = forced; a.qplus = qplus; a.work = c->work;
   a.status = c->status;
   a.real_status = props ? c->rstatus : nullptr;
+  a.hfield = c->hfield;
+  a.chain_of = props ? c->chain_of : nullptr;
   cudaError_t e;
   if (c->work_tc) {
     a.work = c->work_tc;
@@ -627,6 +635,28 @@ tnmc_status tnmc_realization_status(tnmc_ctx* c, int32_t* out_host) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "status copy");
   for (int k = 0; k < c->n_real; ++k) out_host[k] = (st[k] & tnmc::ST_NUMERIC) ? TNMC_ERR_NUMERIC : TNMC_OK;
+  return TNMC_OK;
+}
+
+tnmc_status tnmc_set_fields(tnmc_ctx* c, const int8_t* fields) {
+  if (!c) return fail(nullptr, TNMC_ERR_ARG, "NULL context");
+  if (!fields) {                       // back to no fields (the buffer stays for reuse)
+    c->hfield = nullptr;
+    c->env_built = false;
+    return TNMC_OK;
+  }
+  const size_t nb = (size_t)c->n_real * c->L * c->L;
+  if (!c->hfield_buf) {
+    tnmc_status s = dalloc(c, &c->hfield_buf, nb);
+    if (s) return s;
+  }
+  const bool dev = is_device_ptr(fields);
+  cudaError_t e = cudaMemcpyAsync(c->hfield_buf, fields, nb, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e == cudaSuccess && !dev) e = cudaStreamSynchronize(c->stream);   // the host buffer may go at once
+  if (e != cudaSuccess) return cuda_fail(c, e, "fields copy");
+  c->hfield = c->hfield_buf;
+  c->env_built = false;
   return TNMC_OK;
 }
 
@@ -827,6 +857,26 @@ tnmc_status ctx_enqueue_readback(tnmc_ctx* c, double* acc_h, int64_t* clamps_h, 
 }
 
 int ctx_capacity(const tnmc_ctx* c) { return c->cap; }
+
+tnmc_status ctx_alloc(tnmc_ctx* c, void** p, size_t bytes) { return dalloc(c, p, bytes); }
+
+int8_t* ctx_couplings_dev(tnmc_ctx* c) { return c->J; }
+
+tnmc_status ctx_use_fields_dev(tnmc_ctx* c, int8_t* fields_dev) {
+  c->hfield = fields_dev;
+  c->env_built = false;
+  return TNMC_OK;
+}
+
+void ctx_set_chain_of(tnmc_ctx* c, const int* chain_of_dev) { c->chain_of = chain_of_dev; }
+
+const uint32_t* ctx_packed(const tnmc_ctx* c) { return c->packed; }
+const double* ctx_logq(const tnmc_ctx* c) { return c->logq; }
+const int32_t* ctx_energy(const tnmc_ctx* c) { return c->energy; }
+const unsigned* ctx_realization_status_dev(const tnmc_ctx* c) { return c->rstatus; }
+const int64_t* ctx_clamps_dev(const tnmc_ctx* c) { return c->clamps; }
+int ctx_words(const tnmc_ctx* c) { return c->words; }
+void ctx_add_launches(tnmc_ctx* c, int64_t n) { c->launches += n; }
 
 cudaStream_t ctx_stream(const tnmc_ctx* c) { return c->stream; }
 

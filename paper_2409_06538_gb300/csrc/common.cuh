@@ -9,7 +9,7 @@
 
 namespace tnmc {
 
-enum : uint32_t { PURPOSE_BOND = 0u, PURPOSE_SPIN = 1u, PURPOSE_ACCEPT = 2u };
+enum : uint32_t { PURPOSE_BOND = 0u, PURPOSE_SPIN = 1u, PURPOSE_ACCEPT = 2u, PURPOSE_LINES = 3u };
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of the multiply-xor bijection with
 // the key bumped by the Weyl constants between rounds.

@@ -25,6 +25,24 @@ tnmc_status ctx_enqueue_readback(tnmc_ctx* c, double* acc_h, int64_t* clamps_h, 
 
 int ctx_capacity(const tnmc_ctx* c);
 
+// Device memory owned by the context (released with it), from the same allocator as its buffers.
+tnmc_status ctx_alloc(tnmc_ctx* c, void** p, size_t bytes);
+// Device couplings [real][2L(L-1)] of the context, for a caller that writes them in place
+// (the periodic driver) before tnmc_build_env.
+int8_t* ctx_couplings_dev(tnmc_ctx* c);
+// Use a device array [real][L][L] of external fields (units of beta) owned by the caller.
+tnmc_status ctx_use_fields_dev(tnmc_ctx* c, int8_t* fields_dev);
+// Chain index of each realization's spin draws (device [real]), or nullptr.
+void ctx_set_chain_of(tnmc_ctx* c, const int* chain_of_dev);
+// Outputs of the last tnmc_propose / state of the context, on the device.
+const uint32_t* ctx_packed(const tnmc_ctx* c);
+const double* ctx_logq(const tnmc_ctx* c);
+const int32_t* ctx_energy(const tnmc_ctx* c);
+const unsigned* ctx_realization_status_dev(const tnmc_ctx* c);
+const int64_t* ctx_clamps_dev(const tnmc_ctx* c);
+int ctx_words(const tnmc_ctx* c);
+void ctx_add_launches(tnmc_ctx* c, int64_t n);
+
 // Pinned host memory from a process-wide cache (never handed back with cudaFreeHost while
 // the process runs, so that releasing it cannot synchronise the device).
 void* pinned_get(size_t bytes);

@@ -204,6 +204,9 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
   __shared__ int knext_s;
 
   const int8_t* J = args.J + (size_t)real * 2 * L * (L - 1);
+  // external fields (units of beta) of this realization: the row MPO carries those of the row
+  // below as a site weight exp(beta k s_b), the top-row closure of log Z those of row 0
+  const int8_t* hf = args.hfield ? args.hfield + (size_t)real * L * L : nullptr;
   const int8_t* Jh = J;                          // [r][c], c < L-1
   const int8_t* Jv = J + (size_t)L * (L - 1);    // [r][c], r < L-1
   int* kd = args.kdim + (size_t)real * L * (L + 1);
@@ -253,6 +256,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
         T w = (jv_s[c] * spin_of(x) * spin_of(b) > 0) ? eb : ebm;
         if (c > 0) w *= (jh_s[c - 1] * spin_of(a) * spin_of(b) > 0) ? eb : ebm;
         else if (a == 1) w = T(0);
+        if (hf) { const int k = hf[(size_t)(r + 1) * L + c]; if (k) w *= (T)exp(beta * (double)(k * spin_of(b))); }
         Wc[tid] = w;
       }
     };
@@ -806,8 +810,10 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       const T* row0 = rowbuf;
       double ell[2][E];
       double lsum = 0.0;
-      for (int x = 0; x < 2; ++x)
-        for (int e = 0; e < E; ++e) ell[x][e] = (double)row0[x * CHI * CHI + 0 * CHI + lane + 32 * e];
+      for (int x = 0; x < 2; ++x) {
+        const double h0 = hf ? exp(beta * (double)(hf[0] * spin_of(x))) : 1.0;
+        for (int e = 0; e < E; ++e) ell[x][e] = h0 * (double)row0[x * CHI * CHI + 0 * CHI + lane + 32 * e];
+      }
       for (int c = 1; c < L; ++c) {
         const T* t = row0 + (size_t)c * TILE;
         const double jb = beta * (double)Jh[c - 1];
@@ -825,6 +831,11 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
               const double cf = f0[x] * l0 + f1[x] * l1;
               for (int e = 0; e < E; ++e) nx[x][e] += cf * (double)t[x * CHI * CHI + al * CHI + lane + 32 * e];
             }
+          }
+        if (hf)
+          for (int x = 0; x < 2; ++x) {
+            const double hc = exp(beta * (double)(hf[c] * spin_of(x)));
+            for (int e = 0; e < E; ++e) nx[x][e] *= hc;
           }
         double mx = 0.0;
         for (int x = 0; x < 2; ++x)
@@ -852,7 +863,8 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
     const T* row0 = rowbuf;   // row 0 lives in buffer (0 & 1) = 0
     double ell[2];            // lane holds ell[x][lane] for lane < CHI
     double lsum = 0.0;
-    for (int x = 0; x < 2; ++x) ell[x] = (lane < CHI) ? (double)row0[x * CHI * CHI + 0 * CHI + lane] : 0.0;
+    for (int x = 0; x < 2; ++x)
+      ell[x] = (lane < CHI) ? (hf ? exp(beta * (double)(hf[0] * spin_of(x))) : 1.0) * (double)row0[x * CHI * CHI + 0 * CHI + lane] : 0.0;
     for (int c = 1; c < L; ++c) {
       const T* t = row0 + (size_t)c * TILE;
       const double jb = beta * (double)Jh[c - 1];
@@ -866,6 +878,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
           nx[x] += (f0 * l0 + f1 * l1) * b;
         }
       }
+      if (hf) { nx[0] *= exp(beta * (double)hf[c]); nx[1] *= exp(-beta * (double)hf[c]); }
       double mx = fmax(fabs(nx[0]), fabs(nx[1]));
       mx = warp_max(mx);
       if (mx > 0.0) { nx[0] /= mx; nx[1] /= mx; lsum += log(mx); }

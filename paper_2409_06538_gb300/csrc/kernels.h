@@ -29,6 +29,7 @@ struct EnvBuildArgs {
   long long* stats;       // [real][4]: max Jacobi sweeps, unconverged SVDs, total sweeps, SVDs (nullable)
   unsigned* status;
   T* Mscratch = nullptr;  // [real][D*D] scratch, used only when CHI = 64 (M does not fit in shared memory)
+  const int8_t* hfield = nullptr;   // [real][L][L] external fields in units of beta (weight exp(beta k s)), nullable
 };
 
 template <typename T, typename TE>
@@ -59,6 +60,8 @@ struct SampleArgs {
   void* work;                      // [grid][warps][L][2*CHI] of compute type
   unsigned* status;
   unsigned* real_status;           // [real] per-realization status bits (nullable)
+  const int8_t* hfield;            // [real][L][L] external fields in units of beta (nullable)
+  const int* chain_of;             // [real] chain index of the draws' counters (nullable: item / n)
 };
 
 cudaError_t launch_sample(const SampleArgs& a, int precision, int CHI, int num_sms, cudaStream_t st);

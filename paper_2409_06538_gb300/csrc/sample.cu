@@ -76,7 +76,7 @@ sample_kernel(SampleArgs a) {
     const int k = (int)(tile % tiles_per_real) * NW + warp;
     const bool valid = k < a.n_items;
     const int64_t item = (int64_t)real * a.n_items + k;
-    const int chain = a.forced ? 0 : k / a.n;
+    const int chain = a.forced ? 0 : (a.chain_of ? a.chain_of[real] : k / a.n);
     const uint32_t step = (uint32_t)(a.step0 + (uint64_t)(a.forced ? 0 : k % a.n));
     const uint64_t seed = a.seeds[real];
     const double betad = a.beta[real];
@@ -86,6 +86,7 @@ sample_kernel(SampleArgs a) {
     int8_t* prow = rows + (size_t)warp * 2 * L;      // previous row spins
     int8_t* crow = prow + L;                          // current row spins
     const int8_t* forced = (a.forced && valid) ? a.forced + (size_t)item * N : nullptr;
+    const int8_t* hf = a.hfield ? a.hfield + (size_t)real * N : nullptr;
 
     double logq = 0.0;          // FP64 total
     int energy = 0, magnet = 0;
@@ -132,6 +133,7 @@ sample_kernel(SampleArgs a) {
           const int jh = jh_s[c - 1];
           T f0 = 1, f1 = 1;                     // exp(h_c s_y) for y = 0 (+1), 1 (-1)
           if (r > 0) { const int sg = jv_s[c] * prow[c]; f0 = sg > 0 ? eb : ebm; f1 = sg > 0 ? ebm : eb; }
+          if (hf) { const int kh = hf[(size_t)r * L + c]; if (kh) { f0 *= num<T>::exp_((T)(betad * kh)); f1 *= num<T>::exp_((T)(-betad * kh)); } }
           const T same = jh > 0 ? eb : ebm, diff = jh > 0 ? ebm : eb;
           const T n0 = same * f0 * v0 + diff * f1 * v1;   // y' = +1
           const T n1 = diff * f0 * v0 + same * f1 * v1;   // y' = -1
@@ -166,6 +168,7 @@ sample_kernel(SampleArgs a) {
         T f0 = 1, f1 = 1;
         if (r > 0) { const int sg = jv_s[c] * prow[c]; f0 = sg > 0 ? eb : ebm; f1 = sg > 0 ? ebm : eb; }
         if (c > 0) { const int sg = jh_s[c - 1] * sprev; f0 *= sg > 0 ? eb : ebm; f1 *= sg > 0 ? ebm : eb; }
+        if (hf) { const int kh = hf[(size_t)r * L + c]; if (kh) { f0 *= num<T>::exp_((T)(betad * kh)); f1 *= num<T>::exp_((T)(-betad * kh)); } }
         T w0 = f0 * d0, w1 = f1 * d1;
         if (w0 < T(0)) { w0 = 0; ++nclamp; }
         if (w1 < T(0)) { w1 = 0; ++nclamp; }
@@ -265,7 +268,7 @@ sample_kernel_wide(SampleArgs a) {
     const int k = (int)(tile % tiles_per_real) * NW + warp;
     const bool valid = k < a.n_items;
     const int64_t item = (int64_t)real * a.n_items + k;
-    const int chain = a.forced ? 0 : k / a.n;
+    const int chain = a.forced ? 0 : (a.chain_of ? a.chain_of[real] : k / a.n);
     const uint32_t step = (uint32_t)(a.step0 + (uint64_t)(a.forced ? 0 : k % a.n));
     const uint64_t seed = a.seeds[real];
     const double betad = a.beta[real];
@@ -275,6 +278,7 @@ sample_kernel_wide(SampleArgs a) {
     int8_t* prow = rows + (size_t)warp * 2 * L;      // previous row spins
     int8_t* crow = prow + L;                          // current row spins
     const int8_t* forced = (a.forced && valid) ? a.forced + (size_t)item * N : nullptr;
+    const int8_t* hf = a.hfield ? a.hfield + (size_t)real * N : nullptr;
 
     double logq = 0.0;          // FP64 total
     int energy = 0, magnet = 0;
@@ -336,6 +340,7 @@ sample_kernel_wide(SampleArgs a) {
           const int jh = jh_s[c - 1];
           T f0 = 1, f1 = 1;                     // exp(h_c s_y) for y = 0 (+1), 1 (-1)
           if (r > 0) { const int sg = jv_s[c] * prow[c]; f0 = sg > 0 ? eb : ebm; f1 = sg > 0 ? ebm : eb; }
+          if (hf) { const int kh = hf[(size_t)r * L + c]; if (kh) { f0 *= num<T>::exp_((T)(betad * kh)); f1 *= num<T>::exp_((T)(-betad * kh)); } }
           const T same = jh > 0 ? eb : ebm, diff = jh > 0 ? ebm : eb;
           T n0[E], n1[E], mx = 0;
 #pragma unroll
@@ -382,6 +387,7 @@ sample_kernel_wide(SampleArgs a) {
         T f0 = 1, f1 = 1;
         if (r > 0) { const int sg = jv_s[c] * prow[c]; f0 = sg > 0 ? eb : ebm; f1 = sg > 0 ? ebm : eb; }
         if (c > 0) { const int sg = jh_s[c - 1] * sprev; f0 *= sg > 0 ? eb : ebm; f1 *= sg > 0 ? ebm : eb; }
+        if (hf) { const int kh = hf[(size_t)r * L + c]; if (kh) { f0 *= num<T>::exp_((T)(betad * kh)); f1 *= num<T>::exp_((T)(-betad * kh)); } }
         T w0 = f0 * d0, w1 = f1 * d1;
         if (w0 < T(0)) { w0 = 0; ++nclamp; }
         if (w1 < T(0)) { w1 = 0; ++nclamp; }

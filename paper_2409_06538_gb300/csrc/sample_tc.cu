@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(128) sample_tc_kernel(SampleArgs a) {
     const int k = (int)(tileid % tiles_per_real) * M + tid;
     const bool valid = k < a.n_items;
     const int64_t item = (int64_t)real * a.n_items + k;
-    const int chain = a.forced ? 0 : k / a.n;
+    const int chain = a.forced ? 0 : (a.chain_of ? a.chain_of[real] : k / a.n);
     const uint32_t step = (uint32_t)(a.step0 + (uint64_t)(a.forced ? 0 : k % a.n));
     const uint64_t seed = a.seeds[real];
     const double betad = a.beta[real];
@@ -250,6 +250,7 @@ __global__ void __launch_bounds__(128) sample_tc_kernel(SampleArgs a) {
     const int8_t* J = a.J + (size_t)real * 2 * L * (L - 1);
     const float* envr = reinterpret_cast<const float*>(a.env) + (size_t)real * L * L * TILE;
     const int8_t* forced = (a.forced && valid) ? a.forced + (size_t)item * N : nullptr;
+    const int8_t* hf = a.hfield ? a.hfield + (size_t)real * N : nullptr;
     double logq = 0.0;
     int energy = 0, magnet = 0;
     long long nclamp = 0;
@@ -300,6 +301,7 @@ __global__ void __launch_bounds__(128) sample_tc_kernel(SampleArgs a) {
             const int sg = jv_s[c] * sp;
             f0 = sg > 0 ? eb : ebm; f1 = sg > 0 ? ebm : eb;
           }
+          if (hf) { const int kh = hf[(size_t)r * L + c]; if (kh) { f0 *= expf((float)(betad * kh)); f1 *= expf((float)(-betad * kh)); } }
           const float same = jh > 0 ? eb : ebm, diff = jh > 0 ? ebm : eb;
           float mx = 0.0f;
 #pragma unroll
@@ -366,6 +368,7 @@ __global__ void __launch_bounds__(128) sample_tc_kernel(SampleArgs a) {
           f0 = sg > 0 ? eb : ebm; f1 = sg > 0 ? ebm : eb;
         }
         if (c > 0) { const int sg = jh_s[c - 1] * sprev; f0 *= sg > 0 ? eb : ebm; f1 *= sg > 0 ? ebm : eb; }
+        if (hf) { const int kh = hf[(size_t)r * L + c]; if (kh) { f0 *= expf((float)(betad * kh)); f1 *= expf((float)(-betad * kh)); } }
         float w0 = f0 * d0, w1 = f1 * d1;
         if (w0 < 0.0f) { w0 = 0.0f; ++nclamp; }
         if (w1 < 0.0f) { w1 = 0.0f; ++nclamp; }

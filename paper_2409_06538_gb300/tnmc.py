@@ -210,6 +210,19 @@ class TNMC:
         assert out.is_cuda and out.dtype == torch.int32 and out.numel() >= self.n_real
         self._chk(self.lib.tnmc_realization_status_async(self.ctx, _ptr(out)))
 
+    def set_fields(self, fields):
+        """External fields in units of beta (int8 [R, L, L], host array or cuda tensor; None
+        removes them): the weight gains exp(beta sum k s).  Build the environments again."""
+        if fields is None:
+            self._chk(self.lib.tnmc_set_fields(self.ctx, None))
+            return
+        if isinstance(fields, torch.Tensor):
+            f = fields.contiguous()
+            self._chk(self.lib.tnmc_set_fields(self.ctx, _ptr(f)))
+        else:
+            f = np.ascontiguousarray(np.asarray(fields, dtype=np.int8))
+            self._chk(self.lib.tnmc_set_fields(self.ctx, _c.c_void_p(f.ctypes.data)))
+
     def device_bytes(self):
         return int(self.lib.tnmc_device_bytes(self.ctx))
 
@@ -222,6 +235,78 @@ class TNMC:
     def close(self):
         if getattr(self, "ctx", None):
             self.lib.tnmc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def torus_couplings_pmj(L, seeds, p, stream=None):
+    """Seeded +-J couplings of len(seeds) L x L tori on the device: int8 [R, 2 L^2]."""
+    lib = _capi.load()
+    seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    out = torch.empty((len(seeds), 2 * L * L), dtype=torch.int8, device="cuda")
+    _capi.check(lib.tnmc_torus_couplings_pmj(L, len(seeds), seeds.ctypes.data_as(_capi.c_uint64_p), float(p),
+                                             _ptr(out), _stream_handle(stream)))
+    return out
+
+
+class TNMCPeriodic:
+    """n_real torus realizations sampled with a pinned pair of lines per step (Sec. IV), behind
+    tnmc_periodic_*."""
+
+    def __init__(self, L, couplings, beta, seeds, chi, precision="fp64", n_chains=2, n_therm=0, stream=None,
+                 allocator="torch"):
+        self.lib = _capi.load()
+        self.L, self.chi, self.n_chains = int(L), int(chi), int(n_chains)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+        self.n_real = len(seeds)
+        beta = np.ascontiguousarray(np.broadcast_to(np.asarray(beta, dtype=np.float64), (self.n_real,)))
+        J = couplings.contiguous() if isinstance(couplings, torch.Tensor) else \
+            np.ascontiguousarray(np.asarray(couplings, dtype=np.int8))
+        jp = _c.c_void_p(J.data_ptr() if isinstance(J, torch.Tensor) else J.ctypes.data)
+        opts = _capi.Opts(_capi.PRECISIONS[precision], self.n_chains, int(n_therm), _stream_handle(self.stream))
+        if allocator == "torch":
+            self._alloc = _TorchAllocator(torch.cuda.current_device())
+            opts.alloc, opts.free = self._alloc.alloc, self._alloc.free
+        ctx = _c.c_void_p()
+        code = self.lib.tnmc_periodic_create(self.L, self.n_real, jp, beta.ctypes.data_as(_capi.c_double_p),
+                                             seeds.ctypes.data_as(_capi.c_uint64_p), self.chi, _c.byref(opts),
+                                             _c.byref(ctx))
+        if code != 0:
+            msg = self.lib.tnmc_periodic_last_error(None)
+            raise _capi.TnmcError(code, msg.decode() if msg else "")
+        self.ctx = ctx
+        self._keep = (J, beta, seeds)
+
+    def _chk(self, code):
+        if code != 0:
+            msg = self.lib.tnmc_periodic_last_error(self.ctx)
+            raise _capi.TnmcError(code, msg.decode() if msg else "")
+
+    def step(self, n, step0=0):
+        self._chk(self.lib.tnmc_periodic_step(self.ctx, int(n), int(step0)))
+
+    def spins(self):
+        out = torch.empty((self.n_real, self.n_chains, self.L, self.L), dtype=torch.int8, device="cuda")
+        self._chk(self.lib.tnmc_periodic_get_spins(self.ctx, _ptr(out)))
+        return out
+
+    def observables(self):
+        arr = (_capi.Obs * self.n_real)()
+        self._chk(self.lib.tnmc_periodic_observables(self.ctx, arr))
+        return [{k: getattr(o, k) for k, _ in _capi.Obs._fields_} for o in arr]
+
+    def launch_count(self):
+        return int(self.lib.tnmc_periodic_launch_count(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.tnmc_periodic_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):
