@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle sample")
+    ap.add_argument("--periodic", action="store_true",
+                    help="periodic boundaries (pinned pair of lines per step) on L x L tori: one JSON line")
     ap.add_argument("--serve", action="store_true",
                     help="serving measurement: a Poisson request stream through the request server")
     ap.add_argument("--serve-requests", type=int, default=300)
@@ -255,6 +257,10 @@ def main():
         dist.init_process_group(backend)
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return _finish(world)
+    if a.periodic:
+        if rank == 0:
+            return run_periodic(a)
         return _finish(world)
     if a.serve:
         if rank == 0:
@@ -515,6 +521,51 @@ def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
                              algorithmic_bytes_per_launch=samp_bytes, busy_ms=samp_union_ms,
                              traffic=samp_traffic,
                              peak_source="measured" if "hbm_gbs" in peaks else "fallback"))
+
+
+def run_periodic(a):
+    """Periodic boundaries by a pinned pair of lines (Sec. IV): R tori of side L, --chains chains,
+    --n steps each (one region proposal of (L-1)^2 spins per step and chain, each with its own
+    environment build).  Prints one JSON line: region spins proposed per second, acceptance and
+    the torus observables."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2409_06538_gb300 as tn
+    torch.cuda.set_device(0)
+    beta = tn.nishimori_beta(a.p)
+    seeds = list(range(1000, 1000 + a.R))
+    J = tn.torus_couplings_pmj(a.L, seeds, a.p)
+    ctx = tn.TNMCPeriodic(a.L, J, [beta] * a.R, seeds, a.chi, precision=a.precision, n_chains=a.chains,
+                          n_therm=a.warmup)
+    ctx.step(a.warmup, 0)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launch_count()
+    t0.record()
+    ctx.step(a.n, a.warmup)
+    t1.record()
+    torch.cuda.synchronize()
+    el = t0.elapsed_time(t1) / 1e3
+    ck = clocks.stop()
+    obs = ctx.observables()
+    dav = tn.disorder_average(obs, a.L, beta)
+    spins = a.R * a.chains * a.n * (a.L - 1) ** 2
+    line = dict(metric="region spins proposed/s, periodic boundaries (pinned pair of lines per step)",
+                value=spins / el, unit=UNIT, mode="periodic", n_gpus=1, steps=a.n, warmup=a.warmup,
+                ms_per_step=1e3 * el / a.n, higher_is_better=True, dtype=a.precision, data="synthetic",
+                config=dict(workload=f"periodic TNMC, {a.R} tori of L={a.L}, chi={a.chi}, p={a.p} Nishimori beta, "
+                                     f"{a.chains} chains, {a.n} steps", L=a.L, chi=a.chi, p=a.p, R=a.R,
+                            chains=a.chains, precision=a.precision),
+                gpu_launches=ctx.launch_count() - l0, clocks=ck, acceptance=dav["acceptance"],
+                failed_realizations=dav["n_dropped"],
+                observables={k: dav[k] for k in ("E", "m2", "q2", "U_m", "Q_q")},
+                nishimori_E=-2 * a.L * a.L * (1 - 2 * a.p))
+    ctx.close()
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_serve(a):
