@@ -308,13 +308,7 @@ def test_argument_errors(tn):
     ctx.close()
 
 
-_FP32_L256 = pytest.mark.xfail(strict=True, reason=(
-    "at L = 256 the FP32-built environments with the FP32 tensor-core sweep reach 2.4e-3 - 3.6e-3 at their "
-    "worst sites (99.9th percentile 1.3e-4) against the 1e-3 tolerance (measured)"))
-
-
-@pytest.mark.parametrize("L,seed", [(128, 77), pytest.param(256, 1_000_003, marks=_FP32_L256),
-                                    pytest.param(256, 18_000_068, marks=_FP32_L256)])
+@pytest.mark.parametrize("L,seed", [(128, 77), (256, 1_000_003), (256, 18_000_068)])
 def test_large_lattice_parity_tf32(tn, L, seed):
     """The configuration the throughput is quoted on (chi = 32, p = 0.109, mixed TF32) at L = 128
     and 256: teacher-forced q(+) at every site of the GPU's own proposals within 1e-3 of the FP64
