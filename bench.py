@@ -31,8 +31,8 @@ if ROOT not in sys.path:
 # DRAM bytes per unit of work from one ncu capture of the current kernels (dram__bytes_read.sum +
 # dram__bytes_write.sum at L = 128, chi = 32, 16 realizations x 500 proposals, mixed TF32;
 # profiles/dram_traffic_L128_chi32_R16_tf32.md), scaled by the units of a launch in roofline()
-ENV_DRAM_BYTES_PER_SITE_STEP = (471182336 + 6143689472) / (16 * 127 * 128)              # 25.4 KB
-SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE = (30039463680 + 34397299456) / (16 * 500 * 128 * 128)   # 492 B
+ENV_DRAM_BYTES_PER_SITE_STEP = (304292096 + 6117933568) / (16 * 127 * 128)              # 24.7 KB
+SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE = (29919938048 + 34385152512) / (16 * 500 * 128 * 128)   # 491 B
 
 METRIC = "spins proposed/s at L=256 χ=32, BF16/TF32 vs FP64 GPU path; p50/p99 latency"
 UNIT = "spins/s"
