@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="tf32", choices=["bf16", "tf32", "fp32", "fp64"])
+    ap.add_argument("--compression", default="canonical", choices=["canonical", "zipup"],
+                    help="boundary-MPS compression of the environment build (tnmc_compression)")
     ap.add_argument("--L", type=int, default=256)
     ap.add_argument("--chi", type=int, default=32)
     ap.add_argument("--R", type=int, default=64, help="realizations per GPU")
@@ -156,6 +158,7 @@ def _config(a):
                          f"{a.chains} chains x {a.n} proposals per GPU per step",
                 L=a.L, chi=a.chi, p=a.p, realizations_per_gpu=a.R, chains=a.chains,
                 proposals_per_chain=a.n, precision=("fp64" if a.impl == "reference" else a.precision),
+                compression=("canonical" if a.impl == "reference" else a.compression),
                 l2="inputs larger than L2: the environment cache read by the sampler is rebuilt every step")
 
 
@@ -297,7 +300,7 @@ def main():
     streams = [torch.cuda.Stream(device=dev) for _ in range(S)]
     J0 = tn.couplings_pmj(L, seeds_for(0), a.p)
     ctxs = [tn.TNMC(L, J0, [beta] * R, seeds_for(0), a.chi, precision=a.precision, n_chains=a.chains,
-                    n_therm=0, stream=streams[i]) for i in range(S)]
+                    n_therm=0, stream=streams[i], compression=a.compression) for i in range(S)]
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     # per timed batch, the realizations' failure flags (copied on the device after the
@@ -474,7 +477,7 @@ def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
     implementation's iterations): Householder QR of the 4chi x 2chi matrix ~27 chi^3, the MPO
     product R A ~32 chi^3, the truncating SVD of the 2chi x 2chi matrix ~100 chi^3 and the
     product carrying the truncated state on ~16 chi^3, i.e. 175 chi^3 flops, times (L-1) L site
-    steps per realization.  It runs on the FP32 (FP64) CUDA cores, so the peak is the ALU peak
+    steps per realization (the zip-up compression has no QR: 148 chi^3).  It runs on the FP32 (FP64) CUDA cores, so the peak is the ALU peak
     derived from 152 SMs x 128 FP32 lanes x 2 flops x the SM clock (a 64th of it for FP64).
     Sampling sweep: bytes of the environment tiles read twice per row per 128-proposal tile plus
     the per-site workspace written and read back, against the measured HBM copy bandwidth."""
@@ -486,7 +489,7 @@ def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
     hbm = peaks.get("hbm_gbs", 6800.0)
     L, chi = a.L, a.chi
     CHI = 4 if chi <= 4 else 8 if chi <= 8 else 16 if chi <= 16 else 32 if chi <= 32 else 64
-    site_flops = 175.0 * chi ** 3
+    site_flops = (148.0 if getattr(a, "compression", "canonical") == "zipup" else 175.0) * chi ** 3
     build_flops = a.R * (L - 1) * L * site_flops                  # per launch (one batch)
     K = len(marks)
     sm_clock = peaks.get("sm_max_mhz", 2070.0) * 1e6
@@ -503,7 +506,8 @@ def roofline(a, marks, build_union_ms, samp_union_ms, mean_sweeps):
     samp_gbs = K * samp_bytes / (samp_union_ms / 1e3) / 1e9
     env_traffic = samp_traffic = None
     if a.precision == "tf32" and CHI == 32:
-        if ENV_DRAM_BYTES_PER_SITE_STEP is not None:
+        # the counters were taken on the canonical build; the zip-up build writes no R factors
+        if ENV_DRAM_BYTES_PER_SITE_STEP is not None and getattr(a, "compression", "canonical") == "canonical":
             env_traffic = ENV_DRAM_BYTES_PER_SITE_STEP * a.R * (L - 1) * L
         if SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE is not None:
             samp_traffic = SAMPLE_TC_DRAM_BYTES_PER_PROPOSAL_SITE * a.R * items * L * L

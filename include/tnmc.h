@@ -74,6 +74,22 @@ typedef enum {
 typedef void* (*tnmc_alloc_fn)(size_t bytes, void* stream, void* user);
 typedef void (*tnmc_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 
+/* Compression of the boundary MPS (the environment build). */
+typedef enum {
+  TNMC_COMPRESS_CANONICAL = 0,  /* Sec. II.B: per row, a left-to-right QR sweep (R factors of the left
+                                   parts) and a right-to-left truncating SVD sweep (the SVD QR-
+                                   preconditioned); the best truncation at a given chi */
+  TNMC_COMPRESS_ZIPUP = 1       /* zip-up: per row one truncating SVD sweep and no QR sweep.  It
+                                   relies on the previous row being canonical on the side the sweep
+                                   reaches last, so the sweep direction alternates: the row built
+                                   from the bond-1 last row sweeps left to right, the next right to
+                                   left, and so on.  A left-to-right row is computed as the
+                                   right-to-left sweep of the mirrored row (sites reversed, bonds
+                                   swapped, each horizontal bond factor at the bond's right site).
+                                   Cheaper per site and less accurate at the same chi (lower
+                                   acceptance); not available through tnmc_build_env_noalloc */
+} tnmc_compression;
+
 typedef struct {
   int precision;      /* tnmc_precision */
   int n_chains;       /* Markov chains (replicas) per realization, >= 1; the overlap q of
@@ -83,6 +99,7 @@ typedef struct {
   tnmc_alloc_fn alloc;   /* caller's device allocator, or NULL (then free must be NULL too) */
   tnmc_free_fn free;
   void* alloc_user;      /* passed to alloc and free unchanged */
+  int compression;       /* tnmc_compression; 0 (zero-initialised options) is the canonical one */
 } tnmc_opts;
 
 /* Per-realization thermal means over measured steps (Sec. III.C).  m = (1/N) sum_i s_i,

@@ -91,6 +91,39 @@ def compress(A, chi):
     return A, logs
 
 
+def compress_zipup(A, chi):
+    """Zip-up compression of the MPO x MPS product A, right to left: one truncating SVD sweep
+    and no canonicalising QR sweep.  At site c the truncated right part already found is
+    contracted into A[c] and the min(chi, rows, cols) largest singular values of the result are
+    kept; the sweep relies on the input MPS being left-canonical, so that the part it has not
+    reached is close to an isometry (the MPO spoils that a little, which is the approximation).
+    Returns (normalised right-canonical MPS, log of the removed scale)."""
+    Lx = len(A)
+    out = [None] * Lx
+    logs = 0.0
+    C = np.ones((1, 1))
+    for c in range(Lx - 1, 0, -1):
+        T = np.einsum('lxd,dk->lxk', A[c], C)                 # (D_left, 2, k_right)
+        Dl, _, kr = T.shape
+        U, S, Vh = np.linalg.svd(T.reshape(Dl, 2 * kr), full_matrices=False)
+        k = min(chi, S.shape[0])
+        out[c] = Vh[:k].reshape(k, 2, kr)
+        C = U[:, :k] * S[:k]
+        nrm = np.linalg.norm(C)
+        C = C / nrm
+        logs += np.log(nrm)
+    T = np.einsum('lxd,dk->lxk', A[0], C)
+    nrm = np.linalg.norm(T)
+    out[0] = T / nrm
+    return out, logs + np.log(nrm)
+
+
+def mirror(mps):
+    """The same row vector with the sites in reverse order: site c becomes site Lx-1-c and its
+    bonds swap."""
+    return [b.transpose(2, 1, 0) for b in reversed(mps)]
+
+
 class Envs:
     """Cached row environments: B[r][c] (k_c, 2, k_{c+1}), lam[r], log_z, and the external
     fields H (Ly, Lx) the network was built with (None: no fields)."""
@@ -111,9 +144,19 @@ class Envs:
         return [b.shape[0] for b in self.B[r]] + [1]
 
 
-def build_envs(Jh, Jv, beta, chi, H=None):
+def build_envs(Jh, Jv, beta, chi, H=None, method="canonical"):
     """All row environments of the Ly x Lx lattice (Jh (Ly, Lx-1), Jv (Ly-1, Lx)), optionally
-    with external fields H (Ly, Lx): the weight of a configuration gains exp(sum H s)."""
+    with external fields H (Ly, Lx): the weight of a configuration gains exp(sum H s).
+
+    method "canonical": the QR sweep + truncating SVD sweep of Sec. II.B (compress).
+    method "zipup": compress_zipup, alternating the sweep direction from row to row so that
+    every row's input is canonical on the side the sweep reaches last: the row built from the
+    exact bond-1 last row sweeps left to right (its result is left-canonical), the next one
+    right to left, and so on.  A left-to-right row is the right-to-left sweep of the mirrored
+    row: reversed couplings (so each horizontal bond factor sits at the bond's right site
+    instead of its left one), the mirrored input, and the result mirrored back."""
+    if method not in ("canonical", "zipup"):
+        raise ValueError(method)
     Jh = np.asarray(Jh, dtype=np.float64)
     Jv = np.asarray(Jv, dtype=np.float64)
     H = None if H is None else np.asarray(H, dtype=np.float64)
@@ -122,8 +165,16 @@ def build_envs(Jh, Jv, beta, chi, H=None):
     lam = np.zeros(Ly)
     B[Ly - 1] = [np.ones((1, 2, 1)) for _ in range(Lx)]
     for r in range(Ly - 2, -1, -1):
-        A = apply_mpo(row_mpo(beta, Jv[r], Jh[r + 1], None if H is None else H[r + 1]), B[r + 1])
-        B[r], lam[r] = compress(A, chi)
+        h = None if H is None else H[r + 1]
+        if method == "canonical":
+            B[r], lam[r] = compress(apply_mpo(row_mpo(beta, Jv[r], Jh[r + 1], h), B[r + 1]), chi)
+        elif (Ly - 2 - r) % 2 == 1:
+            B[r], lam[r] = compress_zipup(apply_mpo(row_mpo(beta, Jv[r], Jh[r + 1], h), B[r + 1]), chi)
+        else:
+            A = apply_mpo(row_mpo(beta, Jv[r][::-1], Jh[r + 1][::-1], None if h is None else h[::-1]),
+                          mirror(B[r + 1]))
+            Bm, lam[r] = compress_zipup(A, chi)
+            B[r] = mirror(Bm)
     log_z = float(lam.sum()) + log_row_sum(B[0], Jh[0], beta, None if H is None else H[0])
     return Envs(B, lam, log_z, Jh, Jv, beta, chi, H)
 

@@ -73,9 +73,12 @@ ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
 
 
+COMPRESSIONS = {"canonical": 0, "zipup": 1}
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("n_chains", c_int), ("n_therm", c_int), ("stream", c_void_p),
-                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", c_void_p)]
+                ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", c_void_p), ("compression", c_int)]
 
 
 class Obs(ctypes.Structure):

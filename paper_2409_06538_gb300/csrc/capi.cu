@@ -44,6 +44,7 @@ struct tnmc_ctx {
   unsigned* status = nullptr;
   unsigned* rstatus = nullptr;    // per-realization status bits (numeric failures of its proposals)
   int8_t* hfield = nullptr;       // external fields in units of beta, [real][L][L] (nullptr: none)
+  int compression = TNMC_COMPRESS_CANONICAL;
   int8_t* hfield_buf = nullptr;   // the buffer behind hfield, allocated at the first tnmc_set_fields
   const int* chain_of = nullptr;  // chain index of each realization's draws (periodic driver), or nullptr
   // sampling
@@ -267,6 +268,8 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
     return fail(nullptr, TNMC_ERR_UNSUPPORTED, "the FP64 path is built for chi <= 32 (chi = 64 needs 256 KB of shared memory)");
   if (opts->precision < 0 || opts->precision > 3) return fail(nullptr, TNMC_ERR_ARG, "unknown precision");
   if (opts->n_chains < 1 || opts->n_chains > 8) return fail(nullptr, TNMC_ERR_ARG, "n_chains must be in [1, 8]");
+  if (opts->compression != TNMC_COMPRESS_CANONICAL && opts->compression != TNMC_COMPRESS_ZIPUP)
+    return fail(nullptr, TNMC_ERR_ARG, "unknown compression");
   if ((opts->alloc == nullptr) != (opts->free == nullptr))
     return fail(nullptr, TNMC_ERR_ARG, "opts.alloc and opts.free must be given together");
   for (int k = 0; k < n_real; ++k)
@@ -284,6 +287,7 @@ tnmc_status tnmc_create(int L, int n_real, const int8_t* couplings, const double
   tnmc_ctx* c = new tnmc_ctx();
   c->L = L; c->n_real = n_real; c->cap = n_real; c->chi = chi; c->CHI = round_chi(chi);
   c->precision = opts->precision; c->n_chains = opts->n_chains; c->n_therm = opts->n_therm;
+  c->compression = opts->compression;
   c->stream = reinterpret_cast<cudaStream_t>(opts->stream);
   c->words = (L * L + 31) / 32;
   cudaGetDevice(&c->device);
@@ -421,6 +425,7 @@ tnmc_status tnmc_build_env(tnmc_ctx* c, double* log_z_host) {
       tnmc::EnvBuildArgs<double, double> a{c->L, c->n_real, c->chi, c->J, c->beta, (double*)c->env, c->kdim, c->dqr,
                                            c->lam, c->logz, (double*)c->rowbuf, (double*)c->Rstore, c->stats, c->status};
       a.hfield = c->hfield;
+      a.zipup = c->compression == TNMC_COMPRESS_ZIPUP;
       e = tnmc::launch_env_build(a, c->CHI, c->stream);
       break;
     }
@@ -429,6 +434,7 @@ tnmc_status tnmc_build_env(tnmc_ctx* c, double* log_z_host) {
                                                  c->dqr, c->lam, c->logz, (float*)c->rowbuf, (float*)c->Rstore, c->stats, c->status};
       a.Mscratch = (float*)c->mscratch;
       a.hfield = c->hfield;
+      a.zipup = c->compression == TNMC_COMPRESS_ZIPUP;
       e = tnmc::launch_env_build(a, c->CHI, c->stream);
       break;
     }
@@ -437,6 +443,7 @@ tnmc_status tnmc_build_env(tnmc_ctx* c, double* log_z_host) {
                                          c->lam, c->logz, (float*)c->rowbuf, (float*)c->Rstore, c->stats, c->status};
       a.Mscratch = (float*)c->mscratch;
       a.hfield = c->hfield;
+      a.zipup = c->compression == TNMC_COMPRESS_ZIPUP;
       e = tnmc::launch_env_build(a, c->CHI, c->stream);
     }
   }

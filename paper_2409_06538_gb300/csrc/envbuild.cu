@@ -369,22 +369,35 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
     const int* kold = kd + (size_t)(r + 1) * (L + 1);
     int* knew = kd + (size_t)r * (L + 1);
 
-    // QR bond dimensions d_c of the MPO x MPS (left-canonical form)
+    // Zip-up rows alternate their sweep direction; a left-to-right row runs as the right-to-left
+    // sweep of the mirrored row.  The backward sweep below works in the sweep's frame: frame site
+    // f is site osite(f) of the lattice, whose bonds are swapped when the row is mirrored.
+    const bool zip = args.zipup != 0;
+    const bool mir = zip && ((L - 2 - r) % 2 == 0);
+    auto osite = [&](int f) { return mir ? L - 1 - f : f; };
+    // canonical: QR bond dimensions d_c of the MPO x MPS (left-canonical form); zip-up: the
+    // rows of frame site f's matrix M, (MPO bond) x (previous row's bond into f)
     if (tid == 0) {
-      dqr[0] = 1;
-      for (int c = 0; c < L - 1; ++c) dqr[c + 1] = min(2 * dqr[c], 2 * kold[c + 1]);
+      if (zip) {
+        for (int f = 0; f < L; ++f) dqr[f] = (f == 0 ? 1 : 2) * (mir ? kold[L - f] : kold[f]);
+      } else {
+        dqr[0] = 1;
+        for (int c = 0; c < L - 1; ++c) dqr[c + 1] = min(2 * dqr[c], 2 * kold[c + 1]);
+      }
     }
     for (int c = tid; c < L; c += NT) jv_s[c] = Jv[(size_t)r * L + c];
     for (int c = tid; c < L - 1; c += NT) jh_s[c] = Jh[(size_t)(r + 1) * (L - 1) + c];
-    // W(x,a,b) of site c from exp(+-beta): the vertical bond to the row below and the
-    // horizontal bond of the row below (absent at c = 0, where only a = 0 exists)
+    // W(x,a,b) of (frame) site c from exp(+-beta): the vertical bond to the row below and the
+    // horizontal bond of the row below to the previous frame site (absent at c = 0, where only
+    // a = 0 exists) -- in a mirrored row that is the bond to the lattice site on the right
     auto set_w = [&](int c) {
       if (tid < 8) {
         const int x = tid >> 2, a = (tid >> 1) & 1, b = tid & 1;
-        T w = (jv_s[c] * spin_of(x) * spin_of(b) > 0) ? eb : ebm;
-        if (c > 0) w *= (jh_s[c - 1] * spin_of(a) * spin_of(b) > 0) ? eb : ebm;
+        const int co = osite(c);
+        T w = (jv_s[co] * spin_of(x) * spin_of(b) > 0) ? eb : ebm;
+        if (c > 0) w *= (jh_s[mir ? co : c - 1] * spin_of(a) * spin_of(b) > 0) ? eb : ebm;
         else if (a == 1) w = T(0);
-        if (hf) { const int k = hf[(size_t)(r + 1) * L + c]; if (k) w *= (T)exp(beta * (double)(k * spin_of(b))); }
+        if (hf) { const int k = hf[(size_t)(r + 1) * L + co]; if (k) w *= (T)exp(beta * (double)(k * spin_of(b))); }
         Wc[tid] = w;
       }
     };
@@ -394,11 +407,12 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
     if (!kBig && tid == 0) {
       for (int e = 0; e < D * D; ++e) Rstore[e] = (e == 0) ? T(1) : T(0);
     }
-    if constexpr (!kBig) prefetch_async(Bt, prev, TILE * (int)sizeof(T), tid, NT);      // tile of site 0
+    // the tile the first sweep starts on: site 0 (forward sweep), frame site L-1 (zip-up)
+    if constexpr (!kBig) prefetch_async(Bt, prev + (size_t)(zip ? osite(L - 1) : 0) * TILE, TILE * (int)sizeof(T), tid, NT);
     __syncthreads();
 
-    // ---------------- forward sweep: R factors of the left parts ----------------
-    for (int c = 0; c < L - 1; ++c) {
+    // ---------------- forward sweep: R factors of the left parts (canonical only) ----------------
+    for (int c = 0; !zip && c < L - 1; ++c) {
       set_w(c);
       if constexpr (kBig) {
         Rc = Rstore + (size_t)c * D * D;
@@ -595,13 +609,15 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       set_w(c);
       if constexpr (kBig) {
         Rc = Rstore + (size_t)c * D * D;
-        Bt = const_cast<T*>(prev + (size_t)c * TILE);
+        Bt = const_cast<T*>(prev + (size_t)osite(c) * TILE);
       }
       cp_async_wait_env();
       __syncthreads();
-      // Q[b][al][g] = sum_be B[b][al][be] P[(b,be)][g]: 4 x 4 register tiles
+      // Q[b][al][g] = sum_be B[b][al][be] P[(b,be)][g]: 4 x 4 register tiles (a mirrored row
+      // reads the previous row's tile with its bonds swapped)
       {
         constexpr int TA = CHI / 4;
+        const int sA = mir ? 1 : CHI, sB = mir ? CHI : 1;
         for (int u = tid; u < 2 * TA * TA; u += NT) {
           const int b = u / (TA * TA), a0 = ((u % (TA * TA)) % TA) * 4, g0 = ((u % (TA * TA)) / TA) * 4;
           T acc[4][4] = {};
@@ -610,7 +626,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
             for (int be = 0; be < CHI; ++be) {
               T bv[4], pv[4];
 #pragma unroll
-              for (int ii = 0; ii < 4; ++ii) bv[ii] = Bt[b * CHI * CHI + (a0 + ii) * CHI + be];
+              for (int ii = 0; ii < 4; ++ii) bv[ii] = Bt[b * CHI * CHI + (a0 + ii) * sA + be * sB];
 #pragma unroll
               for (int jj = 0; jj < 4; ++jj) pv[jj] = Ps[(g0 + jj) * D + b * CHI + be];
 #pragma unroll
@@ -629,7 +645,7 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
         }
       }
       __syncthreads();
-      if (!kBig && c > 0) prefetch_async(Bt, prev + (size_t)(c - 1) * TILE, TILE * (int)sizeof(T), tid, NT);
+      if (!kBig && c > 0) prefetch_async(Bt, prev + (size_t)osite(c - 1) * TILE, TILE * (int)sizeof(T), tid, NT);
       const int n = 2 * kn;    // compact columns j = x*kn + g
       // M[(a,al)][j] = sum_b W(x,a,b) Q[b][al][g]
       for (int e = tid; e < D * n; e += NT) {
@@ -650,20 +666,31 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
         __syncthreads();
         const T nrm = red[0];
         const T inv = nrm > T(0) ? T(1) / nrm : T(0);
+        T* ctile0 = cur + (size_t)osite(0) * TILE;
+        TE* etile0 = erow + (size_t)osite(0) * TILE;
         for (int e = tid; e < TILE; e += NT) {
-          const int y = e / (CHI * CHI), al = (e / CHI) % CHI, be = e % CHI;
+          const int y = e / (CHI * CHI), i = (e / CHI) % CHI, j = e % CHI;
+          const int al = mir ? j : i, be = mir ? i : j;     // frame bonds of lattice entry (i, j)
           const T v = (al == 0 && be < kn) ? Mc[(size_t)(y * kn + be) * D] * inv : T(0);
-          cur[e] = v;
-          erow[e] = env_store<TE, T>(v);
+          ctile0[e] = v;
+          etile0[e] = env_store<TE, T>(v);
         }
-        if (tid == 0) { logs += log((double)nrm); knew[0] = 1; }
+        if (tid == 0) { logs += log((double)nrm); knew[0] = 1; knew[L] = 1; }
         __syncthreads();
         break;
       }
       // Y = R_c M  (D x n; R_c, the R factor of the left part up to site c-1, was
-      // prefetched): 4 x 4 register tiles over (rows, compact columns)
+      // prefetched): 4 x 4 register tiles over (rows, compact columns).  Zip-up: Y = M (the
+      // previous row is canonical on the side not yet swept, so no R factor)
       T fro = 0;
-      {
+      if (zip) {
+        for (int e = tid; e < DP * n; e += NT) {
+          const int i = e % DP, j = e / DP;
+          const T v = i < D ? Mc[(size_t)j * D + i] : T(0);
+          Yc[e] = v;
+          fro += v * v;
+        }
+      } else {
         constexpr int TI = D / 4;
         const int TJ = (n + 3) / 4;
         for (int u = tid; u < TI * TJ; u += NT) {
@@ -709,7 +736,13 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
       }
       __syncthreads();
       const T tinyY = red[NWARP] * num<T>::eps * num<T>::eps;
-      {
+      if (zip) {
+        // the zip-up's Y = M is graded by columns (P = U S), where the one-sided Jacobi is
+        // accurate without preconditioning
+        for (int e = tid; e < DP * npad; e += NT) { const int i = e % DP, j = e / DP; Vc[e] = (i == j) ? T(1) : T(0); }
+        for (int e = tid; e < DP * (npad - n); e += NT) Yc[(size_t)n * DP + e] = T(0);
+        __syncthreads();
+      } else {
         // Preconditioning: Y = Q1 R1 (Householder, R1 n x n), R1^T = Q2 R2, so that
         // R1 = R2^T Q2^T and the right singular vectors of Y are V = Q2 Z with Z those of R2^T.
         // The Jacobi then runs on R2^T, whose columns are already close to orthogonal and
@@ -885,9 +918,9 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
         for (int i = 0; i < n; ++i) { const T si = sig[i]; rank += (si > sj) || (si == sj && i < tid); }
         if (rank < k) sel[rank] = tid;
       }
-      if (tid == 0) { knew[c] = k; knext_s = k; }
+      if (tid == 0) { knew[mir ? L - c : c] = k; knext_s = k; }
       __syncthreads();
-      {
+      if (!zip) {
         // V_k = Q2 Z_sel = H_0 H_1 ... H_{n-1} Z_sel: each warp takes its selected columns into
         // registers, applies the reflectors from the last to the first, and writes the result to
         // column g of V (the selection becomes the identity)
@@ -943,10 +976,11 @@ env_build_kernel(EnvBuildArgs<T, TE> args) {
         if (!kBig && c > 1) prefetch_async(Rc, Rstore + (size_t)(c - 1) * D * D, D * D * (int)sizeof(T), tid, NT);
       }
       // B_r[c][y][al][be] = V[(y,be)][sel[al]]
-      T* ctile = cur + (size_t)c * TILE;
-      TE* etile = erow + (size_t)c * TILE;
+      T* ctile = cur + (size_t)osite(c) * TILE;
+      TE* etile = erow + (size_t)osite(c) * TILE;
       for (int e = tid; e < TILE; e += NT) {
-        const int y = e / (CHI * CHI), al = (e / CHI) % CHI, be = e % CHI;
+        const int y = e / (CHI * CHI), i = (e / CHI) % CHI, j = e % CHI;
+        const int al = mir ? j : i, be = mir ? i : j;       // frame bonds of lattice entry (i, j)
         T v = T(0);
         if (al < k && be < kn) v = Vc[(size_t)sel[al] * DP + y * kn + be];
         ctile[e] = v;

@@ -30,6 +30,7 @@ struct EnvBuildArgs {
   unsigned* status;
   T* Mscratch = nullptr;  // [real][D*D] scratch, used only when CHI = 64 (M does not fit in shared memory)
   const int8_t* hfield = nullptr;   // [real][L][L] external fields in units of beta (weight exp(beta k s)), nullable
+  int zipup = 0;                    // 1: zip-up compression (tnmc_compression), else canonical
 };
 
 template <typename T, typename TE>

@@ -70,9 +70,10 @@ class TNMC:
     """n_real realizations of one (L, chi) bucket behind one library context."""
 
     def __init__(self, L, couplings, beta, seeds, chi, precision="fp64", n_chains=2, n_therm=0, stream=None,
-                 allocator="torch"):
+                 allocator="torch", compression="canonical"):
         """allocator: "torch" -- device buffers come from PyTorch's caching allocator through the
-        library's allocator hooks; "library" -- the library allocates them itself."""
+        library's allocator hooks; "library" -- the library allocates them itself.
+        compression: "canonical" (QR + SVD sweeps) or "zipup" (tnmc_compression)."""
         self.lib = _capi.load()
         self.L, self.chi, self.n_chains = int(L), int(chi), int(n_chains)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -88,6 +89,7 @@ class TNMC:
         self._keep = (J, beta, seeds)
         opts = _capi.Opts(_capi.PRECISIONS[precision], self.n_chains, int(n_therm),
                           _stream_handle(self.stream))
+        opts.compression = _capi.COMPRESSIONS[compression]
         if allocator == "torch":
             # kept alive with the context: the library calls it until tnmc_destroy
             self._alloc = _TorchAllocator(torch.cuda.current_device())
