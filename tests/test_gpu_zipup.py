@@ -31,9 +31,12 @@ def _zip_envs(seed, L, p, chi, H=None):
     return bm.build_envs(Jh, Jv, beta, chi, H, method="zipup")
 
 
+# Cases are chosen with a gap at the cut: at L = 13, chi = 5 (seed 3) a near-degenerate pair of
+# singular values is split, and the oracle itself moves by 4e-5 in q(+) between two LAPACK SVD
+# drivers, so no FP64 tolerance applies there; chi = 7 on the same lattice agrees to 5e-13.
 @pytest.mark.parametrize("precision,L,chi,fields", [
     ("fp64", 8, 16, False),          # nothing truncated
-    ("fp64", 12, 8, False), ("fp64", 13, 5, False), ("fp64", 16, 16, False), ("fp64", 12, 8, True),
+    ("fp64", 12, 8, False), ("fp64", 13, 7, False), ("fp64", 16, 16, False), ("fp64", 12, 8, True),
     ("fp32", 16, 8, False), ("tf32", 24, 16, False), ("tf32", 20, 32, False),
     ("fp32", 16, 64, False),         # the chi = 64 build (M in global scratch)
 ])
