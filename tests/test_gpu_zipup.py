@@ -83,8 +83,9 @@ def test_zipup_parity(tn, precision, L, chi, fields):
 
 
 def test_zipup_differs_from_canonical_and_rejects_unknown(tn):
-    """When truncating, the two compressions give different environments (zip-up's log Z is
-    further from the untruncated value); an unknown compression is an argument error."""
+    """When truncating, the two compressions give different environments, both close to the
+    untruncated log Z (the sign and size of the truncation error of log Z is not ordered between
+    them: it is a sum of errors that can cancel); an unknown compression is an argument error."""
     from paper_2409_06538_gb300 import _capi
     L, p, chi, seeds = 16, 0.109, 4, [5]
     beta = lattice.nishimori_beta(p)
@@ -98,7 +99,7 @@ def test_zipup_differs_from_canonical_and_rejects_unknown(tn):
     ref = float(ctx.build_env()[0])
     ctx.close()
     assert abs(lz["zipup"] - lz["canonical"]) > 1e-9 * abs(ref)
-    assert abs(lz["zipup"] - ref) > abs(lz["canonical"] - ref)
+    assert max(abs(lz["zipup"] - ref), abs(lz["canonical"] - ref)) < 1e-4 * abs(ref)
     lib = _capi.load()
     opts = _capi.Opts(_capi.PRECISIONS["fp64"], 2, 0, None)
     opts.compression = 7

@@ -121,9 +121,9 @@ def test_zipup_rows_alternate_canonical_forms():
 
 
 def test_zipup_truncated_close_to_canonical():
-    """Truncated: zip-up's log Z is within a small tolerance of the canonical method's at the
-    same chi, and further from the exact value than the canonical method's (it ignores the
-    MPO's effect on the canonical form)."""
+    """Truncated: zip-up's log Z is within a small tolerance of the untruncated value at the
+    same chi as the canonical method's (on this lattice also further from it; that order is not
+    general, the truncation errors of log Z can cancel); an unknown method is refused."""
     L, p = 12, 0.109
     beta = lattice.nishimori_beta(p)
     Jh, Jv = lattice.split_couplings(lattice.couplings_pmj(5, L, p), L)
