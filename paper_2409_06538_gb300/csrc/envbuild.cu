@@ -19,6 +19,10 @@
 //          the normalised remainder; lam_r = log of the removed scale.
 // This is the QR-sweep + truncating-SVD-sweep compression of the oracle, computed without
 // forming Q: the truncated MPS is the same up to gauge (and rounding).
+// Zip-up mode (args.zipup, a compression variant): no forward sweep and Y = M, the Jacobi on M
+// itself (graded by columns); the rows alternate their sweep direction, a left-to-right row
+// running as this backward sweep over the mirrored row (frame site f = lattice site L-1-f,
+// bonds swapped, horizontal bond factors at the bond's right site).
 #include "common.cuh"
 #include "kernels.h"
 
