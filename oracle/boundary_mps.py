@@ -154,8 +154,11 @@ def build_envs(Jh, Jv, beta, chi, H=None, method="canonical"):
     exact bond-1 last row sweeps left to right (its result is left-canonical), the next one
     right to left, and so on.  A left-to-right row is the right-to-left sweep of the mirrored
     row: reversed couplings (so each horizontal bond factor sits at the bond's right site
-    instead of its left one), the mirrored input, and the result mirrored back."""
-    if method not in ("canonical", "zipup"):
+    instead of its left one), the mirrored input, and the result mirrored back.
+    method "sitewise": the contraction order of Fig. fig:contraction read literally -- the T
+    tensors of every row absorbed one at a time from the right, the bond truncated by SVD at
+    each absorption, no canonical form -- i.e. compress_zipup right to left on every row."""
+    if method not in ("canonical", "zipup", "sitewise"):
         raise ValueError(method)
     Jh = np.asarray(Jh, dtype=np.float64)
     Jv = np.asarray(Jv, dtype=np.float64)
@@ -168,7 +171,7 @@ def build_envs(Jh, Jv, beta, chi, H=None, method="canonical"):
         h = None if H is None else H[r + 1]
         if method == "canonical":
             B[r], lam[r] = compress(apply_mpo(row_mpo(beta, Jv[r], Jh[r + 1], h), B[r + 1]), chi)
-        elif (Ly - 2 - r) % 2 == 1:
+        elif method == "sitewise" or (Ly - 2 - r) % 2 == 1:
             B[r], lam[r] = compress_zipup(apply_mpo(row_mpo(beta, Jv[r], Jh[r + 1], h), B[r + 1]), chi)
         else:
             A = apply_mpo(row_mpo(beta, Jv[r][::-1], Jh[r + 1][::-1], None if h is None else h[::-1]),

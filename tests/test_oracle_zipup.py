@@ -134,3 +134,31 @@ def test_zipup_truncated_close_to_canonical():
         assert dz < 1e-2 * abs(ref) and dc <= dz
     with pytest.raises(ValueError):
         bm.build_envs(Jh, Jv, beta, 4, method="variational")
+
+
+@pytest.mark.parametrize("L,seed", [(4, 3), (4, 11)])
+def test_sitewise_untruncated_is_exact(L, seed):
+    """The literal site-by-site reading (right to left on every row, no canonical form) is exact
+    when nothing is truncated: log Z equals enumeration."""
+    beta = 0.7
+    Jh, Jv = lattice.split_couplings(lattice.couplings_pmj(seed, L, 0.25), L)
+    _, _, logZ, _ = brute.exact(Jh, Jv, beta)
+    assert abs(bm.build_envs(Jh, Jv, beta, 2 ** L, method="sitewise").log_z - logZ) < 1e-12 * abs(logZ)
+
+
+def test_sitewise_rows_right_canonical():
+    """Every row of the literal site-by-site reading is swept right to left: right-canonical,
+    the norm at site 0; rows after the first equal no zip-up row (the input's canonical side is
+    the wrong one)."""
+    L, chi = 8, 4
+    beta = lattice.nishimori_beta(0.109)
+    Jh, Jv = lattice.split_couplings(lattice.couplings_pmj(4, L, 0.109), L)
+    e = bm.build_envs(Jh, Jv, beta, chi, method="sitewise")
+    for r in range(L - 1):
+        B = e.B[r]
+        for c in range(1, L):
+            M = B[c].reshape(B[c].shape[0], -1)
+            assert np.abs(M @ M.T - np.eye(M.shape[0])).max() < 1e-12
+        assert abs(np.linalg.norm(B[0]) - 1.0) < 1e-12
+    z = bm.build_envs(Jh, Jv, beta, chi, method="zipup")
+    assert abs(z.log_z - e.log_z) > 1e-9 * abs(z.log_z)
